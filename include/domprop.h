@@ -1,0 +1,159 @@
+/*
+ * domprop.h -- C ABI of the GB300 domain-propagation library (libdomprop.so).
+ *
+ * The library tightens variable bounds of a system of linear constraints
+ *
+ *     lhs <= A x <= rhs,      lb <= x <= ub,      x_j integer for some j
+ *
+ * (Eq. 1 of Sofranac, Gleixner, Pokutta, "Accelerating Domain Propagation:
+ * an Efficient GPU-Parallel Algorithm over Sparse Matrices", arXiv 2009.07785)
+ * by round-synchronous domain propagation (Alg. 2 of that paper): every
+ * round computes each row's minimum and maximum activity (Def. 1, Eq. 2a/2b)
+ * with infinite contributions counted apart (Sec. 3.4), derives a bound
+ * candidate for every nonzero from the row's residual activity (Eq. 3a/3b in
+ * the residual form of Eq. 5a/5b), rounds integer candidates (Step 3), and
+ * applies candidates that improve a bound by more than a threshold
+ * (Sec. 1.1, last paragraph; Sec. 3.5) with atomic min/max.  Rounds repeat on
+ * the device, with no host synchronisation between rounds, until a round
+ * changes nothing, detects infeasibility (Step 2, or crossing bounds), or a
+ * round cap is reached (Sec. 4.1 uses 100).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: >= 0 on success (see each function), a negative DP_ERR_*
+ *     code on failure.  No C++ exception crosses this boundary.
+ *   - Infinite bounds and sides: IEEE +-inf, or any value whose magnitude is
+ *     >= params.inf_threshold.
+ *   - All floating-point data is IEEE binary64; all arithmetic on the device
+ *     is binary64 as well.
+ *   - Pointers documented as "host or device" may point to host memory
+ *     (pageable or pinned) or to device memory of the context's GPU; the
+ *     library detects which with cudaPointerGetAttributes.
+ *   - The library never frees or retains caller memory.
+ *   - Calls on one dp_ctx are not thread-safe: serialise them.
+ */
+#ifndef DOMPROP_H
+#define DOMPROP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------- */
+#define DP_OK 0
+#define DP_CAP_HIT 1             /* success, but the round cap was hit    */
+#define DP_ERR_INVALID_ARG (-1)  /* null pointer, bad size, bad params     */
+#define DP_ERR_BAD_CSR (-2)      /* malformed CSR, column out of range,
+                                    zero / NaN / infinite coefficient      */
+#define DP_ERR_NAN_INPUT (-3)    /* NaN in lb, ub, lhs or rhs, or lb=+inf,
+                                    ub=-inf, lhs=+inf, rhs=-inf            */
+#define DP_ERR_OOM (-4)          /* device or host allocation failed       */
+#define DP_ERR_CUDA (-5)         /* a CUDA runtime call failed             */
+#define DP_ERR_TIMEOUT (-6)      /* a bounded device wait gave up          */
+
+typedef struct dp_ctx dp_ctx;       /* one GPU + one stream + scratch      */
+typedef struct dp_matrix dp_matrix; /* a constraint matrix resident on GPU */
+
+/*
+ * Tolerances and limits.  The paper fixes only the round cap (100, Sec. 4.1);
+ * the other values are readings of passages that name a threshold without a
+ * value (Sec. 1.1 last paragraph: improvement threshold; Step 3: rounding of
+ * integer bounds).  dp_params_default() fills in:
+ *   max_rounds    = 100
+ *   eps_int       = 1e-6   integer candidates: ceil(c - eps_int) for lower,
+ *                          floor(c + eps_int) for upper bounds
+ *   tau_rel       = 1e-6   a continuous candidate c is applied to a lower
+ *                          bound l iff l == -inf or c > l + tau_rel*max(1,|l|)
+ *                          (upper bounds mirrored); integer candidates must
+ *                          be strictly better
+ *   eps_feas      = 1e-6   Step 2 / crossing tolerance eps_feas*max(1,|v|)
+ *   inf_threshold = 1e20   |v| >= inf_threshold means infinite
+ */
+typedef struct {
+  int32_t max_rounds;
+  int32_t reserved0;
+  double eps_int;
+  double tau_rel;
+  double eps_feas;
+  double inf_threshold;
+} dp_params;
+
+/* Fills *out with the defaults above.  Returns DP_OK or DP_ERR_INVALID_ARG
+ * if out is NULL. */
+int dp_params_default(dp_params *out);
+
+/* Human-readable text for a return code; never NULL, static storage. */
+const char *dp_strerror(int code);
+
+/*
+ * Creates a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t; NULL means the context creates and owns a
+ * non-blocking stream).  The caller keeps ownership of a stream it passes
+ * and must keep it alive until dp_destroy.
+ * Returns DP_OK, DP_ERR_INVALID_ARG, DP_ERR_CUDA or DP_ERR_OOM.
+ */
+int dp_create(dp_ctx **out, int device, void *cuda_stream);
+
+/* Destroys a context (and its stream, if the context created it).  Every
+ * matrix loaded through it must have been freed first.  NULL is a no-op. */
+void dp_destroy(dp_ctx *ctx);
+
+/*
+ * Copies a CSR matrix (Sec. 3: row_ptr / col_idx / val) to the GPU and
+ * builds the device layout (the one-time preprocessing that Sec. 4.3
+ * excludes from timing: rows cut into chunks, chunks sorted by length and
+ * stored as 32-wide slices).  All three arrays are HOST pointers:
+ *   row_ptr[m+1]  int64, row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz
+ *   col_idx[nnz]  int32 in [0, n)
+ *   val[nnz]      finite, nonzero binary64 coefficients
+ * Limits: 0 <= m, n < 2^31; 0 <= nnz < 2^31.
+ * `chunk` is the longest row piece one thread reduces (0 = default 256;
+ * otherwise 8..4096).  Longer rows are split across threads and combined in
+ * a second pass.
+ * On success *out owns device memory until dp_matrix_free.
+ * Returns DP_OK, DP_ERR_INVALID_ARG, DP_ERR_BAD_CSR, DP_ERR_OOM, DP_ERR_CUDA.
+ */
+int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                   const int64_t *row_ptr, const int32_t *col_idx,
+                   const double *val, int32_t chunk, dp_matrix **out);
+
+/* Frees a matrix; NULL is a no-op. */
+void dp_matrix_free(dp_matrix *mat);
+
+/* Shape of a loaded matrix (any pointer may be NULL). */
+int dp_matrix_info(const dp_matrix *mat, int32_t *m, int32_t *n,
+                   int64_t *nnz, int64_t *padded_slots, int32_t *split_rows);
+
+/*
+ * Propagates one problem over a loaded matrix (Alg. 2, round-synchronous).
+ * Inputs (host or device, all binary64 unless noted; not modified):
+ *   lb[n], ub[n]      variable bounds
+ *   vartype[n]        uint8: 0 = continuous, nonzero = integer
+ *   lhs[m], rhs[m]    row sides
+ *   params            NULL = dp_params_default()
+ * Outputs (host or device, caller-allocated, written on success and on
+ * infeasibility; never aliased with inputs):
+ *   lb_out[n], ub_out[n]  bounds after the last executed round
+ *   infeasible            HOST int32: 1 if Step 2 or crossing bounds
+ *                         detected infeasibility (the run stops after the
+ *                         detecting round), else 0
+ *   rounds                HOST int32: executed rounds, counting the final
+ *                         round that found no change
+ * Integer variables' input bounds are rounded (ceil(lb-eps_int),
+ * floor(ub+eps_int)) before round 1.
+ * Blocks until results are available (the stream is synchronised once, at
+ * the end).  Returns DP_OK (converged, or infeasible), DP_CAP_HIT (the last
+ * round still changed a bound when max_rounds rounds had run), or an error.
+ */
+int dp_propagate(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
+                 const double *ub, const uint8_t *vartype, const double *lhs,
+                 const double *rhs, const dp_params *params, double *lb_out,
+                 double *ub_out, int32_t *infeasible, int32_t *rounds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOMPROP_H */

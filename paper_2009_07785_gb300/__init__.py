@@ -1,0 +1,223 @@
+"""GB300 domain propagation (arXiv 2009.07785) -- Python binding of libdomprop.
+
+Thin ctypes marshalling over the C ABI declared in ``include/domprop.h``; the
+functions keep the C names.  Every step of the propagation runs in the CUDA
+library: if ``_lib/libdomprop.so`` is missing this module raises instead of
+falling back to anything else.
+
+Inputs may be numpy arrays (host memory) or torch tensors (host or CUDA);
+outputs are allocated on the same side as ``lb`` unless given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_lib" / "libdomprop.so"
+
+DP_OK = 0
+DP_CAP_HIT = 1
+DP_ERR_INVALID_ARG = -1
+DP_ERR_BAD_CSR = -2
+DP_ERR_NAN_INPUT = -3
+DP_ERR_OOM = -4
+DP_ERR_CUDA = -5
+DP_ERR_TIMEOUT = -6
+
+# exported symbols, in header order
+SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
+           "dp_matrix_free", "dp_matrix_info", "dp_propagate")
+
+
+class dp_params(C.Structure):
+    _fields_ = [("max_rounds", C.c_int32), ("reserved0", C.c_int32), ("eps_int", C.c_double),
+                ("tau_rel", C.c_double), ("eps_feas", C.c_double), ("inf_threshold", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads libdomprop.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(str(LIB_PATH))
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    L.dp_params_default.argtypes = [C.POINTER(dp_params)]
+    L.dp_params_default.restype = C.c_int
+    L.dp_strerror.argtypes = [C.c_int]
+    L.dp_strerror.restype = C.c_char_p
+    L.dp_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+    L.dp_create.restype = C.c_int
+    L.dp_destroy.argtypes = [vp]
+    L.dp_destroy.restype = None
+    L.dp_matrix_load.argtypes = [vp, i32, i32, i64, vp, vp, vp, i32, C.POINTER(vp)]
+    L.dp_matrix_load.restype = C.c_int
+    L.dp_matrix_free.argtypes = [vp]
+    L.dp_matrix_free.restype = None
+    L.dp_matrix_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
+                                 C.POINTER(i64), C.POINTER(i32)]
+    L.dp_matrix_info.restype = C.c_int
+    L.dp_propagate.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp,
+                               C.POINTER(i32), C.POINTER(i32)]
+    L.dp_propagate.restype = C.c_int
+    _lib = L
+    return L
+
+
+class DomPropError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {dp_strerror(code)} ({code})")
+        self.code = code
+
+
+def dp_strerror(code: int) -> str:
+    return lib().dp_strerror(int(code)).decode()
+
+
+def dp_params_default(**overrides) -> dp_params:
+    p = dp_params()
+    lib().dp_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise DomPropError(rc, where)
+    return rc
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+class Context:
+    """A dp_ctx: one GPU and the stream all library work is issued on."""
+
+    def __init__(self, device: int = 0, stream=None):
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        _check(lib().dp_create(C.byref(h), int(device), C.c_void_p(stream) if stream else None),
+               "dp_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().dp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def dp_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def dp_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+class Matrix:
+    """A dp_matrix: a CSR constraint matrix resident on the GPU."""
+
+    def __init__(self, ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int = 0):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib().dp_matrix_load(ctx.handle, int(m), int(n), int(row_ptr[-1]) if m > 0 else 0,
+                                    _ptr(row_ptr), _ptr(col_idx), _ptr(val), int(chunk),
+                                    C.byref(h)), "dp_matrix_load")
+        self.handle = h
+        self.ctx = ctx
+        self.m, self.n = int(m), int(n)
+
+    def info(self) -> dict:
+        m, n, s = C.c_int32(), C.c_int32(), C.c_int32()
+        nnz, pad = C.c_int64(), C.c_int64()
+        _check(lib().dp_matrix_info(self.handle, C.byref(m), C.byref(n), C.byref(nnz),
+                                    C.byref(pad), C.byref(s)), "dp_matrix_info")
+        return {"m": m.value, "n": n.value, "nnz": nnz.value, "padded_slots": pad.value,
+                "split_rows": s.value}
+
+    def close(self):
+        if self.handle:
+            lib().dp_matrix_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def dp_matrix_load(ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int = 0) -> Matrix:
+    return Matrix(ctx, m, n, row_ptr, col_idx, val, chunk)
+
+
+def dp_matrix_free(mat: Matrix) -> None:
+    mat.close()
+
+
+def dp_matrix_info(mat: Matrix) -> dict:
+    return mat.info()
+
+
+@dataclass
+class Result:
+    lb: object
+    ub: object
+    infeasible: int
+    rounds: int
+    status: int  # DP_OK or DP_CAP_HIT
+
+
+def _like(x, n):
+    if isinstance(x, np.ndarray):
+        return np.empty(n, dtype=np.float64)
+    import torch
+    return torch.empty(n, dtype=torch.float64, device=x.device)
+
+
+def dp_propagate(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs, params: dp_params | None = None,
+                 lb_out=None, ub_out=None) -> Result:
+    """Runs round-synchronous propagation to its fixed point (or the cap)."""
+    n = mat.n
+    if lb_out is None:
+        lb_out = _like(lb, n)
+    if ub_out is None:
+        ub_out = _like(lb, n)
+    inf, rounds = C.c_int32(), C.c_int32()
+    rc = _check(lib().dp_propagate(ctx.handle, mat.handle, _ptr(lb), _ptr(ub), _ptr(vartype),
+                                   _ptr(lhs), _ptr(rhs), C.byref(params) if params is not None else None,
+                                   _ptr(lb_out), _ptr(ub_out), C.byref(inf), C.byref(rounds)),
+                "dp_propagate")
+    return Result(lb_out, ub_out, inf.value, rounds.value, rc)

@@ -1,0 +1,359 @@
+// C ABI of libdomprop.so (declared in include/domprop.h).
+//
+// One dp_propagate call: inputs are copied (host) or read in place (device)
+// by a prologue kernel that normalises them into the matrix's workspace;
+// then a CUDA graph runs the propagation rounds of Alg. 2 (arXiv 2009.07785)
+// under a WHILE conditional node whose condition the last kernel of each
+// round sets on the device (the role of the paper's gpu_loop, Sec. 3.7,
+// without a one-thread driver kernel); an epilogue decodes the bounds; the
+// stream is synchronised once.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dp_internal.h"
+#include "dp_launch.h"
+#include "../../include/domprop.h"
+
+struct dp_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  dp::Ctrl *h_ctrl = nullptr;  // pinned mirror of the device control block
+  int live_matrices = 0;
+};
+
+struct dp_matrix {
+  dp_ctx *ctx = nullptr;
+  dp::DevMatrix M{};
+  dp::DevState S{};
+  int64_t padded = 0;
+  std::vector<void *> allocs;
+  uint8_t *vt_ws = nullptr;
+  // staging for host inputs / outputs
+  double *st_lb = nullptr, *st_ub = nullptr, *st_lhs = nullptr, *st_rhs = nullptr;
+  uint8_t *st_vt = nullptr;
+  double *out_lb = nullptr, *out_ub = nullptr;
+  // the round loop
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+#define CUDA_TRY(x)                          \
+  do {                                       \
+    cudaError_t e_ = (x);                    \
+    if (e_ != cudaSuccess) return DP_ERR_CUDA; \
+  } while (0)
+
+template <typename T>
+int dev_alloc(dp_matrix *mat, T **p, size_t count) {
+  void *q = nullptr;
+  size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA;
+  }
+  mat->allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return DP_OK;
+}
+
+template <typename T>
+int upload(dp_matrix *mat, const std::vector<T> &v, const T **out, cudaStream_t st) {
+  T *d = nullptr;
+  int rc = dev_alloc(mat, &d, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  *out = d;
+  return DP_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Makes the round-loop graph of a matrix: one WHILE node whose body is the
+// round's kernels; the condition starts at 1 on every launch.
+int build_graph(dp_matrix *mat) {
+  dp_ctx *ctx = mat->ctx;
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return DP_ERR_CUDA;
+  }
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return DP_ERR_CUDA;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return DP_ERR_CUDA;
+  }
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t le = dp::launch_round_body(mat->M, mat->S, mat->vt_ws, h, ctx->num_sms, cs);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (le != cudaSuccess) e = le;
+  }
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return DP_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return DP_ERR_CUDA;
+  }
+  mat->graph = g;
+  mat->exec = ex;
+  return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dp_params_default(dp_params *out) {
+  if (!out) return DP_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->max_rounds = 100;
+  out->eps_int = 1e-6;
+  out->tau_rel = 1e-6;
+  out->eps_feas = 1e-6;
+  out->inf_threshold = 1e20;
+  return DP_OK;
+}
+
+const char *dp_strerror(int code) {
+  switch (code) {
+    case DP_OK: return "ok";
+    case DP_CAP_HIT: return "round cap hit (bounds valid)";
+    case DP_ERR_INVALID_ARG: return "invalid argument";
+    case DP_ERR_BAD_CSR: return "malformed CSR matrix or invalid coefficient";
+    case DP_ERR_NAN_INPUT: return "NaN or contradictory infinity in bounds or sides";
+    case DP_ERR_OOM: return "out of memory";
+    case DP_ERR_CUDA: return "CUDA runtime error";
+    case DP_ERR_TIMEOUT: return "bounded device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int dp_create(dp_ctx **out, int device, void *cuda_stream) {
+  if (!out) return DP_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return DP_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return DP_ERR_INVALID_ARG;
+  CUDA_TRY(cudaSetDevice(device));
+  dp_ctx *ctx = new (std::nothrow) dp_ctx();
+  if (!ctx) return DP_ERR_OOM;
+  ctx->device = device;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return DP_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return DP_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaMallocHost(&ctx->h_ctrl, sizeof(dp::Ctrl)) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return DP_ERR_OOM;
+  }
+  *out = ctx;
+  return DP_OK;
+}
+
+void dp_destroy(dp_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+void dp_matrix_free(dp_matrix *mat) {
+  if (!mat) return;
+  cudaSetDevice(mat->ctx->device);
+  cudaStreamSynchronize(mat->ctx->stream);
+  if (mat->exec) cudaGraphExecDestroy(mat->exec);
+  if (mat->graph) cudaGraphDestroy(mat->graph);
+  for (void *p : mat->allocs) cudaFree(p);
+  mat->ctx->live_matrices--;
+  delete mat;
+}
+
+int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                   const int64_t *row_ptr, const int32_t *col_idx,
+                   const double *val, int32_t chunk, dp_matrix **out) {
+  if (!ctx || !out) return DP_ERR_INVALID_ARG;
+  *out = nullptr;
+  dp::HostLayout H;
+  int rc = dp::build_layout(m, n, nnz, row_ptr, col_idx, val, chunk, H);
+  if (rc) return rc;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  dp_matrix *mat = new (std::nothrow) dp_matrix();
+  if (!mat) return DP_ERR_OOM;
+  mat->ctx = ctx;
+  ctx->live_matrices++;
+  cudaStream_t st = ctx->stream;
+  dp::DevMatrix &M = mat->M;
+  M.m = m;
+  M.n = n;
+  M.nnz = nnz;
+  M.nslices = H.nslices;
+  M.nslices_split = H.nslices_split;
+  M.nsplit_rows = H.nsplit_rows;
+  mat->padded = (int64_t)H.val.size();
+#define TRY(x)                 \
+  do {                         \
+    int r_ = (x);              \
+    if (r_) {                  \
+      dp_matrix_free(mat);     \
+      return r_;               \
+    }                          \
+  } while (0)
+  TRY(upload(mat, H.val, &M.val, st));
+  TRY(upload(mat, H.col, &M.col, st));
+  TRY(upload(mat, H.slice_off, &M.slice_off, st));
+  TRY(upload(mat, H.slice_len, &M.slice_len, st));
+  TRY(upload(mat, H.chunk_row, &M.chunk_row, st));
+  TRY(upload(mat, H.chunk_len, &M.chunk_len, st));
+  TRY(upload(mat, H.chunk_sidx, &M.chunk_sidx, st));
+  TRY(upload(mat, H.split_row, &M.split_row, st));
+  TRY(upload(mat, H.split_cbeg, &M.split_cbeg, st));
+  dp::DevState &S = mat->S;
+  TRY(dev_alloc(mat, &S.rec, (size_t)n));
+  TRY(dev_alloc(mat, &S.keys, 2 * (size_t)n));
+  TRY(dev_alloc(mat, &S.lhs, (size_t)m));
+  TRY(dev_alloc(mat, &S.rhs, (size_t)m));
+  TRY(dev_alloc(mat, &S.part, (size_t)H.nslices_split * dp::kSliceW));
+  TRY(dev_alloc(mat, &S.rowtot, (size_t)H.nsplit_rows));
+  TRY(dev_alloc(mat, &S.ctrl, 1));
+  TRY(dev_alloc(mat, &mat->vt_ws, (size_t)n));
+  TRY(dev_alloc(mat, &mat->st_lb, (size_t)n));
+  TRY(dev_alloc(mat, &mat->st_ub, (size_t)n));
+  TRY(dev_alloc(mat, &mat->st_vt, (size_t)n));
+  TRY(dev_alloc(mat, &mat->st_lhs, (size_t)m));
+  TRY(dev_alloc(mat, &mat->st_rhs, (size_t)m));
+  TRY(dev_alloc(mat, &mat->out_lb, (size_t)n));
+  TRY(dev_alloc(mat, &mat->out_ub, (size_t)n));
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    dp_matrix_free(mat);
+    return DP_ERR_CUDA;
+  }
+  TRY(build_graph(mat));
+#undef TRY
+  *out = mat;
+  return DP_OK;
+}
+
+int dp_matrix_info(const dp_matrix *mat, int32_t *m, int32_t *n, int64_t *nnz,
+                   int64_t *padded_slots, int32_t *split_rows) {
+  if (!mat) return DP_ERR_INVALID_ARG;
+  if (m) *m = mat->M.m;
+  if (n) *n = mat->M.n;
+  if (nnz) *nnz = mat->M.nnz;
+  if (padded_slots) *padded_slots = mat->padded;
+  if (split_rows) *split_rows = mat->M.nsplit_rows;
+  return DP_OK;
+}
+
+int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
+                 const double *ub, const uint8_t *vartype, const double *lhs,
+                 const double *rhs, const dp_params *params, double *lb_out,
+                 double *ub_out, int32_t *infeasible, int32_t *rounds) {
+  if (!ctx || !cmat || !infeasible || !rounds) return DP_ERR_INVALID_ARG;
+  dp_matrix *mat = const_cast<dp_matrix *>(cmat);
+  if (mat->ctx != ctx) return DP_ERR_INVALID_ARG;
+  const int32_t m = mat->M.m, n = mat->M.n;
+  if (n > 0 && (!lb || !ub || !vartype || !lb_out || !ub_out)) return DP_ERR_INVALID_ARG;
+  if (m > 0 && (!lhs || !rhs)) return DP_ERR_INVALID_ARG;
+  dp_params p;
+  if (params) p = *params; else dp_params_default(&p);
+  if (p.max_rounds < 0 || !(p.eps_int >= 0) || !(p.tau_rel >= 0) || !(p.eps_feas >= 0) ||
+      !(p.inf_threshold > 0))
+    return DP_ERR_INVALID_ARG;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+
+  // inputs: device pointers are read in place, host pointers staged
+  const double *d_lb = lb, *d_ub = ub, *d_lhs = lhs, *d_rhs = rhs;
+  const uint8_t *d_vt = vartype;
+  if (n > 0) {
+    if (!is_device_ptr(lb)) { CUDA_TRY(cudaMemcpyAsync(mat->st_lb, lb, 8 * (size_t)n, cudaMemcpyDefault, st)); d_lb = mat->st_lb; }
+    if (!is_device_ptr(ub)) { CUDA_TRY(cudaMemcpyAsync(mat->st_ub, ub, 8 * (size_t)n, cudaMemcpyDefault, st)); d_ub = mat->st_ub; }
+    if (!is_device_ptr(vartype)) { CUDA_TRY(cudaMemcpyAsync(mat->st_vt, vartype, (size_t)n, cudaMemcpyDefault, st)); d_vt = mat->st_vt; }
+  }
+  if (m > 0) {
+    if (!is_device_ptr(lhs)) { CUDA_TRY(cudaMemcpyAsync(mat->st_lhs, lhs, 8 * (size_t)m, cudaMemcpyDefault, st)); d_lhs = mat->st_lhs; }
+    if (!is_device_ptr(rhs)) { CUDA_TRY(cudaMemcpyAsync(mat->st_rhs, rhs, 8 * (size_t)m, cudaMemcpyDefault, st)); d_rhs = mat->st_rhs; }
+  }
+
+  dp::Ctrl *hc = ctx->h_ctrl;
+  std::memset(hc, 0, sizeof(*hc));
+  hc->max_rounds = p.max_rounds;
+  hc->eps_int = p.eps_int;
+  hc->tau_rel = p.tau_rel;
+  hc->eps_feas = p.eps_feas;
+  hc->inf_thr = p.inf_threshold;
+  CUDA_TRY(cudaMemcpyAsync(mat->S.ctrl, hc, sizeof(*hc), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(dp::launch_prologue(mat->S, mat->vt_ws, m, n, d_lb, d_ub, d_vt, d_lhs, d_rhs,
+                               p.eps_int, p.inf_threshold, ctx->num_sms, st));
+  if (p.max_rounds > 0) CUDA_TRY(cudaGraphLaunch(mat->exec, st));
+
+  if (n > 0) {
+    const bool dl = is_device_ptr(lb_out), du = is_device_ptr(ub_out);
+    double *o_lb = dl ? lb_out : mat->out_lb;
+    double *o_ub = du ? ub_out : mat->out_ub;
+    CUDA_TRY(dp::launch_epilogue(mat->S, n, o_lb, o_ub, ctx->num_sms, st));
+    if (!dl) CUDA_TRY(cudaMemcpyAsync(lb_out, o_lb, 8 * (size_t)n, cudaMemcpyDefault, st));
+    if (!du) CUDA_TRY(cudaMemcpyAsync(ub_out, o_ub, 8 * (size_t)n, cudaMemcpyDefault, st));
+  }
+  CUDA_TRY(cudaMemcpyAsync(hc, mat->S.ctrl, sizeof(*hc), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (hc->err) return hc->err;
+  *infeasible = hc->infeasible ? 1 : 0;
+  *rounds = hc->round;
+  if (!hc->infeasible && hc->last_changed && hc->round >= p.max_rounds && p.max_rounds > 0)
+    return DP_CAP_HIT;
+  return DP_OK;
+}
+
+}  // extern "C"

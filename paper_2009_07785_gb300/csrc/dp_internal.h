@@ -1,0 +1,89 @@
+// Internal types shared by the library's host and device sources.
+//
+// Device layout of a loaded matrix ("sliced ELL over row chunks"):
+//   Every row is cut into chunks of at most `chunk` nonzeros (a row that
+//   fits is one chunk).  Chunks of rows that had to be split ("split rows")
+//   come first, grouped by row; the remaining single-chunk rows follow,
+//   sorted by length, longest first.  32 consecutive chunks form a slice,
+//   which one warp processes with one chunk per lane.  A slice stores its
+//   nonzeros slot-major: element (slot k, lane t) of slice s sits at
+//   slice_off[s] + 32*k + t, so the 32 lanes read 32 consecutive values and
+//   32 consecutive column indices per slot.  Within a chunk the slots keep
+//   the row's CSR order.
+#pragma once
+#include <cstdint>
+
+namespace dp {
+
+constexpr int kSliceW = 32;                 // chunks per slice (= warp width)
+constexpr int32_t kLenMask = 0x3FFFFFFF;    // chunk length bits
+constexpr int32_t kExactFlag = 1 << 30;     // row must skip the FP32 screen
+
+// Current bounds of one variable, as gathered by the round kernels: one
+// 32-byte record, fetched with a single 256-bit load per nonzero.
+struct alignas(32) VarRec {
+  double L, U;     // bounds at the start of the round
+  float W;         // upper bound on (U-L) + 2^-40 (|L|+|U|), +inf if unbounded
+  uint32_t flags;  // bit 0: integer variable
+  uint64_t pad;
+};
+static_assert(sizeof(VarRec) == 32, "VarRec must be one 32-byte sector");
+
+// Partial activity of one chunk of a split row.
+struct alignas(16) Partial {
+  double minfin, maxfin;
+  int32_t mininf, maxinf;
+  float T;          // max over the chunk of an upper bound on |a| W
+  int32_t exact;    // the chunk's row must skip the FP32 screen
+};
+
+// Combined activity of one split row, plus the screen thresholds.
+struct alignas(16) RowTot {
+  double minfin, maxfin;
+  int32_t mininf, maxinf;
+  float thr_r, thr_l;  // a nonzero with |a| W <= thr cannot tighten from that side
+  int32_t active;      // some nonzero of the row may yield an accepted candidate
+  int32_t row;
+};
+
+// Device control block of one propagation run.
+struct Ctrl {
+  int32_t round;        // executed rounds
+  int32_t max_rounds;
+  int32_t changed;      // a candidate was accepted in the current round
+  int32_t last_changed; // value of `changed` at the end of the last round
+  int32_t infeasible;
+  int32_t err;          // 0, or a DP_ERR_* code found by the prologue
+  uint32_t blocks_done; // arrival counter of the last kernel of a round
+  int32_t pad;
+  double eps_int, tau_rel, eps_feas, inf_thr;
+};
+
+struct DevMatrix {
+  int32_t m, n;
+  int64_t nnz;
+  int32_t nslices;        // all slices
+  int32_t nslices_split;  // slices [0, nslices_split) hold split-row chunks
+  int32_t nsplit_rows;
+  int32_t pad;
+  const double *val;        // padded slot-major values
+  const int32_t *col;       // padded slot-major column indices
+  const int64_t *slice_off; // [nslices] element offset of each slice
+  const int32_t *slice_len; // [nslices] slots in each slice
+  const int32_t *chunk_row; // [nslices*32] row of each chunk, -1 = padding
+  const int32_t *chunk_len; // [nslices*32] length | kExactFlag
+  const int32_t *chunk_sidx;// [nslices_split*32] split-row index, -1 = none
+  const int32_t *split_row; // [nsplit_rows] row id of each split row
+  const int32_t *split_cbeg;// [nsplit_rows+1] chunk-slot range of each split row
+};
+
+struct DevState {
+  VarRec *rec;          // [n] state at the start of the round
+  long long *keys;      // [2n] next state as order-preserving int64 keys
+  double *lhs, *rhs;    // [m] normalised sides
+  Partial *part;        // [nslices_split*32]
+  RowTot *rowtot;       // [nsplit_rows]
+  Ctrl *ctrl;
+};
+
+}  // namespace dp

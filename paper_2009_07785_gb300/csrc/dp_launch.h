@@ -1,0 +1,45 @@
+// Host-side launchers of the device kernels (dp_kernels.cu) and the host
+// layout builder (dp_layout.cpp), used by the C ABI in dp_capi.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "dp_internal.h"
+
+namespace dp {
+
+cudaError_t launch_prologue(const DevState &S, uint8_t *vt_ws, int32_t m,
+                            int32_t n, const double *lb, const double *ub,
+                            const uint8_t *vartype, const double *lhs,
+                            const double *rhs, double eps_int, double thr,
+                            int num_sms, cudaStream_t st);
+
+cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out,
+                            double *ub_out, int num_sms, cudaStream_t st);
+
+cudaError_t launch_round_body(const DevMatrix &M, const DevState &S,
+                              const uint8_t *vt_ws,
+                              cudaGraphConditionalHandle handle, int num_sms,
+                              cudaStream_t st);
+
+// Host image of the device layout described in dp_internal.h.
+struct HostLayout {
+  int32_t m = 0, n = 0;
+  int64_t nnz = 0;
+  int32_t nslices = 0, nslices_split = 0, nsplit_rows = 0;
+  std::vector<double> val;
+  std::vector<int32_t> col;
+  std::vector<int64_t> slice_off;
+  std::vector<int32_t> slice_len;
+  std::vector<int32_t> chunk_row, chunk_len, chunk_sidx;
+  std::vector<int32_t> split_row, split_cbeg;
+};
+
+// Validates a host CSR matrix and builds its layout.  Returns DP_OK,
+// DP_ERR_INVALID_ARG, DP_ERR_BAD_CSR or DP_ERR_OOM.
+int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                 const int32_t *col_idx, const double *val, int32_t chunk,
+                 HostLayout &out);
+
+}  // namespace dp

@@ -1,0 +1,143 @@
+// One-time host preprocessing of a constraint matrix (the "blocking of the
+// matrix precomputed on the CPU" that Sec. 4.3 of arXiv 2009.07785 excludes
+// from timing): CSR validation, row chunking, length sorting and the
+// slot-major slice image described in dp_internal.h.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dp_launch.h"
+#include "../../include/domprop.h"
+
+namespace dp {
+
+namespace {
+
+// A coefficient outside [2^-120, 2^120] keeps its row out of the binary32
+// screen (the screen's bit-level |a| bound assumes a normal binary32 range).
+bool coef_screenable(double a) {
+  double x = std::fabs(a);
+  return x >= 0x1p-120 && x <= 0x1p120;
+}
+
+struct Chunk {
+  int32_t row;
+  int64_t begin;  // CSR offset of the chunk's first nonzero
+  int32_t len;
+  int32_t flags;  // kExactFlag
+  int32_t sidx;   // split-row index or -1
+};
+
+}  // namespace
+
+int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                 const int32_t *col_idx, const double *val, int32_t chunk,
+                 HostLayout &out) {
+  if (m < 0 || n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return DP_ERR_INVALID_ARG;
+  if (m > 0 && !row_ptr) return DP_ERR_INVALID_ARG;
+  if (nnz > 0 && (!col_idx || !val)) return DP_ERR_INVALID_ARG;
+  if (chunk == 0) chunk = 256;
+  if (chunk < 8 || chunk > 4096) return DP_ERR_INVALID_ARG;
+  if (m > 0) {
+    if (row_ptr[0] != 0 || row_ptr[m] != nnz) return DP_ERR_BAD_CSR;
+    for (int32_t i = 0; i < m; ++i)
+      if (row_ptr[i + 1] < row_ptr[i]) return DP_ERR_BAD_CSR;
+  } else if (nnz != 0) {
+    return DP_ERR_BAD_CSR;
+  }
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (col_idx[k] < 0 || col_idx[k] >= n) return DP_ERR_BAD_CSR;
+    double a = val[k];
+    if (!std::isfinite(a) || a == 0.0) return DP_ERR_BAD_CSR;
+  }
+
+  try {
+    out = HostLayout();
+    out.m = m;
+    out.n = n;
+    out.nnz = nnz;
+    std::vector<int32_t> rowflag(m > 0 ? m : 1, 0);
+    for (int32_t i = 0; i < m; ++i)
+      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+        if (!coef_screenable(val[k])) { rowflag[i] = kExactFlag; break; }
+
+    // split rows first, in row order, pieces in order
+    std::vector<Chunk> chunks;
+    chunks.reserve((size_t)m + (size_t)(nnz / chunk) + 1);
+    int32_t nsplit = 0;
+    for (int32_t i = 0; i < m; ++i) {
+      int64_t len = row_ptr[i + 1] - row_ptr[i];
+      if (len <= chunk) continue;
+      out.split_row.push_back(i);
+      out.split_cbeg.push_back((int32_t)chunks.size());
+      for (int64_t b = 0; b < len; b += chunk) {
+        int64_t e = b + chunk < len ? b + chunk : len;
+        chunks.push_back({i, row_ptr[i] + b, (int32_t)(e - b), rowflag[i], nsplit});
+      }
+      ++nsplit;
+    }
+    out.split_cbeg.push_back((int32_t)chunks.size());
+    out.nsplit_rows = nsplit;
+    // pad the split region to whole slices so no slice mixes both kinds
+    while (chunks.size() % kSliceW) chunks.push_back({-1, 0, 0, 0, -1});
+    const size_t nsplit_chunks = chunks.size();
+
+    // single-chunk rows by length, longest first (counting sort, stable)
+    std::vector<int64_t> cnt((size_t)chunk + 2, 0);
+    for (int32_t i = 0; i < m; ++i) {
+      int64_t len = row_ptr[i + 1] - row_ptr[i];
+      if (len <= chunk) cnt[(size_t)(chunk - len)]++;
+    }
+    std::vector<int64_t> pos((size_t)chunk + 2, 0);
+    for (size_t b = 1; b < pos.size(); ++b) pos[b] = pos[b - 1] + cnt[b - 1];
+    size_t nsingle = (size_t)pos.back();
+    chunks.resize(nsplit_chunks + nsingle);
+    for (int32_t i = 0; i < m; ++i) {
+      int64_t len = row_ptr[i + 1] - row_ptr[i];
+      if (len > chunk) continue;
+      size_t at = nsplit_chunks + (size_t)pos[(size_t)(chunk - len)]++;
+      chunks[at] = {i, row_ptr[i], (int32_t)len, rowflag[i], -1};
+    }
+    while (chunks.size() % kSliceW) chunks.push_back({-1, 0, 0, 0, -1});
+
+    const size_t nslots = chunks.size();
+    out.nslices = (int32_t)(nslots / kSliceW);
+    out.nslices_split = (int32_t)(nsplit_chunks / kSliceW);
+    out.slice_off.resize(out.nslices);
+    out.slice_len.resize(out.nslices);
+    int64_t total = 0;
+    for (int32_t s = 0; s < out.nslices; ++s) {
+      int32_t L = 0;
+      for (int t = 0; t < kSliceW; ++t) {
+        int32_t l = chunks[(size_t)s * kSliceW + t].len;
+        if (l > L) L = l;
+      }
+      out.slice_off[s] = total;
+      out.slice_len[s] = L;
+      total += (int64_t)L * kSliceW;
+    }
+    out.val.assign((size_t)total, 0.0);
+    out.col.assign((size_t)total, 0);
+    out.chunk_row.resize(nslots);
+    out.chunk_len.resize(nslots);
+    out.chunk_sidx.assign(nsplit_chunks, -1);
+    for (size_t c = 0; c < nslots; ++c) {
+      const Chunk &ch = chunks[c];
+      out.chunk_row[c] = ch.row;
+      out.chunk_len[c] = ch.len | ch.flags;
+      if (c < nsplit_chunks) out.chunk_sidx[c] = ch.sidx;
+      int64_t base = out.slice_off[c / kSliceW] + (int64_t)(c % kSliceW);
+      for (int32_t k = 0; k < ch.len; ++k) {
+        out.val[(size_t)(base + (int64_t)k * kSliceW)] = val[ch.begin + k];
+        out.col[(size_t)(base + (int64_t)k * kSliceW)] = col_idx[ch.begin + k];
+      }
+    }
+  } catch (const std::bad_alloc &) {
+    return DP_ERR_OOM;
+  }
+  return DP_OK;
+}
+
+}  // namespace dp

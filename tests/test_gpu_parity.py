@@ -1,0 +1,136 @@
+"""GPU path vs the CPU oracle through the C ABI, element by element.
+
+Two comparison modes:
+  * replay: every GPU round r starts from the GPU's own state after round
+    r-1 (dp_propagate with max_rounds=1) and is compared with the oracle's
+    round from that same state, so differences cannot accumulate;
+  * full run: both sides propagate to the fixed point independently; bounds,
+    round count and the infeasibility flag must agree.
+Tolerances are those of tests/parity.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2009_07785_gb300 import synth
+from parity import compare_bounds
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy() if isinstance(t, torch.Tensor) else t
+
+
+def gpu_full(dp, ctx, mat, inst, params=None, lb=None, ub=None, on_host=False):
+    args = [inst.lb if lb is None else lb, inst.ub if ub is None else ub, inst.vartype, inst.lhs,
+            inst.rhs]
+    if not on_host:
+        args = [dev(a) for a in args]
+    r = dp.dp_propagate(ctx, mat, *args, params=params)
+    return host(r.lb), host(r.ub), r
+
+
+def replay(dp, ctx, mat, inst, orc, max_rounds=100, params=None):
+    """Round-by-round comparison; returns (rounds, ties)."""
+    q = dict(params or {})
+    L, U, lhs, rhs = orc.normalise(inst.m, inst.n, inst.lb, inst.ub, inst.vartype, inst.lhs,
+                                   inst.rhs, q)
+    p1 = dp.dp_params_default(max_rounds=1, **{k: v for k, v in q.items() if k != "max_rounds"})
+    d_vt, d_lhs, d_rhs = dev(inst.vartype), dev(lhs), dev(rhs)
+    ties = 0
+    for r in range(1, max_rounds + 1):
+        res = dp.dp_propagate(ctx, mat, dev(L), dev(U), d_vt, d_lhs, d_rhs, params=p1)
+        o = orc.round_(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, L, U, inst.vartype, lhs,
+                       rhs, q, analysis=True)
+        g_lb, g_ub = host(res.lb), host(res.ub)
+        nbad, nt, det = compare_bounds(g_lb, g_ub, o.lb, o.ub, inst.vartype, o.lb_err, o.ub_err,
+                                       o.lb_tie, o.ub_tie)
+        ties += nt
+        assert nbad == 0, f"round {r}: {nbad} bounds differ: {det}"
+        assert res.rounds == 1
+        if not o.inf_tie:
+            assert res.infeasible == o.infeasible, f"round {r}: infeasible flag differs"
+        assert (res.status == dp.DP_CAP_HIT) == (bool(o.changed) and not o.infeasible), f"round {r}"
+        if o.infeasible or not o.changed:
+            return r, ties
+        L, U = g_lb, g_ub
+    return max_rounds, ties
+
+
+def check_full(dp, ctx, mat, inst, orc, params=None, exact=True, **kw):
+    g_lb, g_ub, r = gpu_full(dp, ctx, mat, inst,
+                             dp.dp_params_default(**params) if params else None, **kw)
+    o = orc.propagate_instance(inst, params)
+    assert r.infeasible == o.infeasible
+    assert r.rounds == o.rounds, (r.rounds, o.rounds)
+    assert (r.status == dp.DP_CAP_HIT) == bool(o.status)
+    if exact:
+        assert np.array_equal(g_lb, o.lb) and np.array_equal(g_ub, o.ub)
+    else:
+        nbad, _, det = compare_bounds(g_lb, g_ub, o.lb, o.ub, inst.vartype)
+        assert nbad == 0, det
+    return r
+
+
+def test_tiny_full_bit_exact(gpu, orc):
+    dp, ctx = gpu
+    inst = synth.tiny()
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        assert mat.info()["split_rows"] == 0
+        r = check_full(dp, ctx, mat, inst, orc, exact=True)
+        assert r.rounds > 2
+
+
+def test_tiny_host_pointers(gpu, orc):
+    dp, ctx = gpu
+    inst = synth.tiny()
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        check_full(dp, ctx, mat, inst, orc, exact=True, on_host=True)
+
+
+def test_tiny_replay_bit_exact(gpu, orc):
+    dp, ctx = gpu
+    inst = synth.tiny()
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        rounds, ties = replay(dp, ctx, mat, inst, orc)
+        assert rounds > 2 and ties == 0
+
+
+@pytest.mark.parametrize("chunk", [8, 16])
+def test_tiny_split_rows(gpu, orc, chunk):
+    """Rows longer than `chunk` are split across lanes and combined."""
+    dp, ctx = gpu
+    inst = synth.tiny(seed=synth.seed_for(0, 7), m=600, n=400)
+    rp = inst.row_ptr
+    # make some rows long so that several chunks and slices are involved
+    rng = np.random.default_rng(5)
+    big = synth.small_random(rng, 300, 400, 60)
+    with dp.Matrix(ctx, big.m, big.n, big.row_ptr, big.col, big.val, chunk) as mat:
+        assert mat.info()["split_rows"] > 0
+        replay(dp, ctx, mat, big, orc)
+        check_full(dp, ctx, mat, big, orc, exact=False)
+    with dp.Matrix(ctx, inst.m, inst.n, rp, inst.col, inst.val, chunk) as mat:
+        replay(dp, ctx, mat, inst, orc)
+
+
+def test_medium_scaled(gpu, orc):
+    dp, ctx = gpu
+    inst = synth.medium(scale=0.1)
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        assert mat.info()["split_rows"] > 0
+        replay(dp, ctx, mat, inst, orc)
+        check_full(dp, ctx, mat, inst, orc, exact=False)
+
+
+def test_large_scaled(gpu, orc):
+    dp, ctx = gpu
+    inst = synth.large(scale=0.02)
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        assert mat.info()["split_rows"] > 0
+        replay(dp, ctx, mat, inst, orc)
+        check_full(dp, ctx, mat, inst, orc, exact=False)
