@@ -152,6 +152,27 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
                  const double *rhs, const dp_params *params, double *lb_out,
                  double *ub_out, int32_t *infeasible, int32_t *rounds);
 
+/*
+ * The same propagation with the round loop driven from the host: after each
+ * round the control block is copied back and the stream synchronised, and
+ * the host decides whether to launch the next round (the cpu_loop variant
+ * of Sec. 3.7, which the paper uses for its main results).  Results are
+ * identical to dp_propagate; it exists to measure the cost of the host
+ * round trip and to time the round's kernels one by one.
+ * kernel_ms (nullable, 4 floats): total milliseconds, measured with CUDA
+ *   events on the context's stream around each launch, of the four round
+ *   kernels in this order: activities + candidates of whole rows, combine of
+ *   split rows, candidates of split rows, per-variable finish.
+ * kernel_launches (nullable, 4 int32): how many times each was launched.
+ * Arguments and return values are otherwise those of dp_propagate.
+ */
+int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
+                          const double *ub, const uint8_t *vartype,
+                          const double *lhs, const double *rhs,
+                          const dp_params *params, double *lb_out,
+                          double *ub_out, int32_t *infeasible, int32_t *rounds,
+                          float *kernel_ms, int32_t *kernel_launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ DP_ERR_TIMEOUT = -6
 
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
-           "dp_matrix_free", "dp_matrix_info", "dp_propagate")
+           "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop")
 
 
 class dp_params(C.Structure):
@@ -69,6 +69,10 @@ def lib() -> C.CDLL:
     L.dp_propagate.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp,
                                C.POINTER(i32), C.POINTER(i32)]
     L.dp_propagate.restype = C.c_int
+    L.dp_propagate_hostloop.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp,
+                                        C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float),
+                                        C.POINTER(i32)]
+    L.dp_propagate_hostloop.restype = C.c_int
     _lib = L
     return L
 
@@ -198,6 +202,11 @@ class Result:
     infeasible: int
     rounds: int
     status: int  # DP_OK or DP_CAP_HIT
+    kernel_ms: tuple | None = None        # host loop only: per-kernel totals
+    kernel_launches: tuple | None = None  # host loop only: per-kernel counts
+
+
+KERNELS = ("round", "combine", "cand_split", "finish")
 
 
 def _like(x, n):
@@ -221,3 +230,24 @@ def dp_propagate(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs, params: d
                                    _ptr(lb_out), _ptr(ub_out), C.byref(inf), C.byref(rounds)),
                 "dp_propagate")
     return Result(lb_out, ub_out, inf.value, rounds.value, rc)
+
+
+def dp_propagate_hostloop(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
+                          params: dp_params | None = None, lb_out=None, ub_out=None,
+                          timing: bool = True) -> Result:
+    """Same result as dp_propagate, with the round loop on the host (one
+    stream synchronisation per round) and per-kernel CUDA-event timings."""
+    n = mat.n
+    if lb_out is None:
+        lb_out = _like(lb, n)
+    if ub_out is None:
+        ub_out = _like(lb, n)
+    inf, rounds = C.c_int32(), C.c_int32()
+    ms = (C.c_float * 4)()
+    cnt = (C.c_int32 * 4)()
+    rc = _check(lib().dp_propagate_hostloop(
+        ctx.handle, mat.handle, _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs), _ptr(rhs),
+        C.byref(params) if params is not None else None, _ptr(lb_out), _ptr(ub_out),
+        C.byref(inf), C.byref(rounds), ms if timing else None, cnt), "dp_propagate_hostloop")
+    return Result(lb_out, ub_out, inf.value, rounds.value, rc,
+                  tuple(ms) if timing else None, tuple(cnt))

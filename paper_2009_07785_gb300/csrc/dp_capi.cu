@@ -295,24 +295,17 @@ int dp_matrix_info(const dp_matrix *mat, int32_t *m, int32_t *n, int64_t *nnz,
   return DP_OK;
 }
 
-int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
-                 const double *ub, const uint8_t *vartype, const double *lhs,
-                 const double *rhs, const dp_params *params, double *lb_out,
-                 double *ub_out, int32_t *infeasible, int32_t *rounds) {
-  if (!ctx || !cmat || !infeasible || !rounds) return DP_ERR_INVALID_ARG;
-  dp_matrix *mat = const_cast<dp_matrix *>(cmat);
-  if (mat->ctx != ctx) return DP_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Stages inputs, writes the control block and runs the prologue.
+int begin_call(dp_ctx *ctx, dp_matrix *mat, const double *lb, const double *ub,
+               const uint8_t *vartype, const double *lhs, const double *rhs,
+               const dp_params &p) {
   const int32_t m = mat->M.m, n = mat->M.n;
-  if (n > 0 && (!lb || !ub || !vartype || !lb_out || !ub_out)) return DP_ERR_INVALID_ARG;
-  if (m > 0 && (!lhs || !rhs)) return DP_ERR_INVALID_ARG;
-  dp_params p;
-  if (params) p = *params; else dp_params_default(&p);
-  if (p.max_rounds < 0 || !(p.eps_int >= 0) || !(p.tau_rel >= 0) || !(p.eps_feas >= 0) ||
-      !(p.inf_threshold > 0))
-    return DP_ERR_INVALID_ARG;
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-
   // inputs: device pointers are read in place, host pointers staged
   const double *d_lb = lb, *d_ub = ub, *d_lhs = lhs, *d_rhs = rhs;
   const uint8_t *d_vt = vartype;
@@ -325,7 +318,6 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
     if (!is_device_ptr(lhs)) { CUDA_TRY(cudaMemcpyAsync(mat->st_lhs, lhs, 8 * (size_t)m, cudaMemcpyDefault, st)); d_lhs = mat->st_lhs; }
     if (!is_device_ptr(rhs)) { CUDA_TRY(cudaMemcpyAsync(mat->st_rhs, rhs, 8 * (size_t)m, cudaMemcpyDefault, st)); d_rhs = mat->st_rhs; }
   }
-
   dp::Ctrl *hc = ctx->h_ctrl;
   std::memset(hc, 0, sizeof(*hc));
   hc->max_rounds = p.max_rounds;
@@ -335,9 +327,17 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
   hc->inf_thr = p.inf_threshold;
   CUDA_TRY(cudaMemcpyAsync(mat->S.ctrl, hc, sizeof(*hc), cudaMemcpyHostToDevice, st));
   CUDA_TRY(dp::launch_prologue(mat->S, mat->vt_ws, m, n, d_lb, d_ub, d_vt, d_lhs, d_rhs,
-                               p.eps_int, p.inf_threshold, ctx->num_sms, st));
-  if (p.max_rounds > 0) CUDA_TRY(cudaGraphLaunch(mat->exec, st));
+                               p.eps_int, p.tau_rel, p.inf_threshold, ctx->num_sms, st));
+  return DP_OK;
+}
 
+// Decodes the bounds into the outputs, reads the control block back and
+// synchronises the stream once.
+int end_call(dp_ctx *ctx, dp_matrix *mat, const dp_params &p, double *lb_out,
+             double *ub_out, int32_t *infeasible, int32_t *rounds) {
+  const int32_t n = mat->M.n;
+  cudaStream_t st = ctx->stream;
+  dp::Ctrl *hc = ctx->h_ctrl;
   if (n > 0) {
     const bool dl = is_device_ptr(lb_out), du = is_device_ptr(ub_out);
     double *o_lb = dl ? lb_out : mat->out_lb;
@@ -354,6 +354,97 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
   if (!hc->infeasible && hc->last_changed && hc->round >= p.max_rounds && p.max_rounds > 0)
     return DP_CAP_HIT;
   return DP_OK;
+}
+
+int check_call(dp_ctx *ctx, const dp_matrix *mat, const double *lb, const double *ub,
+               const uint8_t *vartype, const double *lhs, const double *rhs,
+               const dp_params *params, double *lb_out, double *ub_out,
+               int32_t *infeasible, int32_t *rounds, dp_params *p) {
+  if (!ctx || !mat || !infeasible || !rounds) return DP_ERR_INVALID_ARG;
+  if (mat->ctx != ctx) return DP_ERR_INVALID_ARG;
+  const int32_t m = mat->M.m, n = mat->M.n;
+  if (n > 0 && (!lb || !ub || !vartype || !lb_out || !ub_out)) return DP_ERR_INVALID_ARG;
+  if (m > 0 && (!lhs || !rhs)) return DP_ERR_INVALID_ARG;
+  if (params) *p = *params; else dp_params_default(p);
+  if (p->max_rounds < 0 || !(p->eps_int >= 0) || !(p->tau_rel >= 0) || !(p->eps_feas >= 0) ||
+      !(p->inf_threshold > 0))
+    return DP_ERR_INVALID_ARG;
+  return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
+                 const double *ub, const uint8_t *vartype, const double *lhs,
+                 const double *rhs, const dp_params *params, double *lb_out,
+                 double *ub_out, int32_t *infeasible, int32_t *rounds) {
+  dp_params p;
+  int rc = check_call(ctx, cmat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
+                      infeasible, rounds, &p);
+  if (rc) return rc;
+  dp_matrix *mat = const_cast<dp_matrix *>(cmat);
+  rc = begin_call(ctx, mat, lb, ub, vartype, lhs, rhs, p);
+  if (rc) return rc;
+  if (p.max_rounds > 0) CUDA_TRY(cudaGraphLaunch(mat->exec, ctx->stream));
+  return end_call(ctx, mat, p, lb_out, ub_out, infeasible, rounds);
+}
+
+int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
+                          const double *ub, const uint8_t *vartype,
+                          const double *lhs, const double *rhs,
+                          const dp_params *params, double *lb_out,
+                          double *ub_out, int32_t *infeasible, int32_t *rounds,
+                          float *kernel_ms, int32_t *kernel_launches) {
+  dp_params p;
+  int rc = check_call(ctx, cmat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
+                      infeasible, rounds, &p);
+  if (rc) return rc;
+  dp_matrix *mat = const_cast<dp_matrix *>(cmat);
+  rc = begin_call(ctx, mat, lb, ub, vartype, lhs, rhs, p);
+  if (rc) return rc;
+  cudaStream_t st = ctx->stream;
+  const bool timed = kernel_ms != nullptr;
+  cudaEvent_t ev[8] = {};
+  if (timed) {
+    for (int i = 0; i < 4; ++i) kernel_ms[i] = 0.0f;
+    for (int i = 0; i < 8; ++i)
+      if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+        for (int q = 0; q < i; ++q) cudaEventDestroy(ev[q]);
+        return DP_ERR_CUDA;
+      }
+  }
+  if (kernel_launches)
+    for (int i = 0; i < 4; ++i) kernel_launches[i] = 0;
+  dp::Ctrl *hc = ctx->h_ctrl;
+  int status = DP_OK;
+  for (int32_t r = 0; r < p.max_rounds; ++r) {
+    cudaError_t e = dp::launch_round_kernels(mat->M, mat->S, mat->vt_ws, 0, 0, ctx->num_sms, st,
+                                             timed ? ev : nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, mat->S.ctrl, sizeof(*hc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { status = DP_ERR_CUDA; break; }
+    const bool split = mat->M.nsplit_rows > 0;
+    if (kernel_launches) {
+      kernel_launches[0] += 1;
+      kernel_launches[1] += split;
+      kernel_launches[2] += split;
+      kernel_launches[3] += 1;
+    }
+    if (timed) {
+      float t;
+      for (int k = 0; k < 4; ++k) {
+        if ((k == 1 || k == 2) && !split) continue;
+        if (cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) kernel_ms[k] += t;
+      }
+    }
+    if (hc->err || !hc->last_changed || hc->infeasible) break;
+  }
+  if (timed)
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+  if (status) return status;
+  return end_call(ctx, mat, p, lb_out, ub_out, infeasible, rounds);
 }
 
 }  // extern "C"

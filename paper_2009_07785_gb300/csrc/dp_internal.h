@@ -23,18 +23,26 @@ constexpr int32_t kExactFlag = 1 << 30;     // row must skip the FP32 screen
 // 32-byte record, fetched with a single 256-bit load per nonzero.
 struct alignas(32) VarRec {
   double L, U;     // bounds at the start of the round
-  float W;         // upper bound on (U-L) + 2^-40 (|L|+|U|), +inf if unbounded
+  float WU, WL;    // screen widths for upper / lower candidates (see kernels)
   uint32_t flags;  // bit 0: integer variable
-  uint64_t pad;
+  uint32_t pad;
 };
 static_assert(sizeof(VarRec) == 32, "VarRec must be one 32-byte sector");
 
 // Partial activity of one chunk of a split row.
+// Screen values of a chunk, per side: the largest (T1) and second largest
+// (T2) upper bounds on |a| W over the chunk, and the slot of the largest.
+struct Top2 {
+  float r1, r2, l1, l2;
+  int32_t kr, kl;
+};
+
 struct alignas(16) Partial {
   double minfin, maxfin;
   int32_t mininf, maxinf;
-  float T;          // max over the chunk of an upper bound on |a| W
+  Top2 t;
   int32_t exact;    // the chunk's row must skip the FP32 screen
+  int32_t pad;
 };
 
 // Combined activity of one split row, plus the screen thresholds.

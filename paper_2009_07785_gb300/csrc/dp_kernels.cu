@@ -1,11 +1,12 @@
 // Device kernels of one propagation round (Alg. 2 of arXiv 2009.07785 with
 // round-synchronous semantics) for sm_103a, plus the per-call prologue and
 // epilogue.  All arithmetic that decides a bound is binary64; binary32 is
-// used only in a conservative screen that proves some rows cannot tighten
-// anything (their binary64 work is then skipped, with identical results).
+// used only in a conservative screen that proves that a nonzero cannot yield
+// an accepted candidate (its binary64 candidate work is then skipped; the
+// result is identical).
 //
-// Round structure (all launched from a CUDA graph whose WHILE node repeats
-// the round until k_finish clears the condition -- no host round trip):
+// Round structure (launched from a CUDA graph whose WHILE node repeats the
+// round until k_finish clears the condition -- no host round trip):
 //   k_round      one warp per slice, one lane per chunk: activities of every
 //                chunk (Def. 1, Eq. 2a/2b, Sec. 3.4 infinity counts); for
 //                whole rows also Step 2, the screen, and the candidates
@@ -16,6 +17,11 @@
 //   k_finish     one thread per variable: decode the next state, crossing
 //                test (Sec. 1.1, remark after Step 3), write the records the
 //                next round gathers; the last block decides whether to loop
+//
+// GB300 has little binary64 throughput (about 0.5 T lane-ops/s, the same for
+// any number of active lanes in a warp), so binary64 work is kept lane-dense:
+// the activity sums run one chunk per lane over length-sorted slices, and
+// candidate formulas run 32 at a time from a per-warp work list.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cfloat>
@@ -27,6 +33,10 @@
 namespace dp {
 
 // ---------------------------------------------------------------- helpers --
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ float f_inf() { return __uint_as_float(0x7F800000u); }
 
 __device__ __forceinline__ bool d_isinf(double x) {
   return ((unsigned long long)__double_as_longlong(x) << 1) == 0xFFE0000000000000ull;
@@ -69,7 +79,7 @@ __device__ __forceinline__ float f32_up(double x) {
   bool neg = (hi >> 31) != 0;
   unsigned e = mh >> 20;
   if (e == 0x7FFu) return __uint_as_float((hi & 0x80000000u) | 0x7F800000u);
-  if (e >= 1151u) return neg ? -FLT_MAX : __uint_as_float(0x7F800000u);
+  if (e >= 1151u) return neg ? -FLT_MAX : f_inf();
   if (e < 897u) {
     if (neg) return -0.0f;
     return (mh | lo) ? FLT_MIN : 0.0f;
@@ -81,46 +91,83 @@ __device__ __forceinline__ float f32_up(double x) {
 }
 __device__ __forceinline__ float f32_dn(double x) { return -f32_up(-x); }
 
-// Upper bound on |a| as binary32 for |a| in [2^-126, 2^127); rows holding a
-// coefficient outside [2^-120, 2^120] are flagged on the host and never use
-// this value.
+// Upper bound on |a| as binary32, exact when |a| is a binary32 value, for
+// |a| in [2^-126, 2^127); rows holding a coefficient outside [2^-120, 2^120]
+// are flagged on the host and never use this value.
 __device__ __forceinline__ float absup_fast(double a) {
   unsigned long long b = (unsigned long long)__double_as_longlong(a);
   unsigned mh = (unsigned)(b >> 32) & 0x7FFFFFFFu, lo = (unsigned)b;
-  return __uint_as_float((((mh << 3) | (lo >> 29)) - (896u << 23)) + 1u);
+  unsigned t = ((mh << 3) | (lo >> 29)) - (896u << 23);
+  return __uint_as_float(t + ((lo & 0x1FFFFFFFu) != 0u));
 }
 
-// Upper bound on max(0, (U-L) + 2^-40 (|L|+|U|)) in binary32 (+inf if
-// unbounded).  The 2^-40 term absorbs the rounding of the binary64 candidate
-// formulas, so that the screen below stays sound even with tau_rel =
-// eps_int = 0.  Clamping at 0 keeps |a|_up * W an upper bound when the
-// bounds cross within the feasibility tolerance (U < L).
-__device__ __forceinline__ float width_up(double L, double U) {
-  float w = __fsub_ru(f32_up(U), f32_dn(L));
-  float mg = __fmul_ru(0x1p-40f, __fadd_ru(f32_up(d_abs(L)), f32_up(d_abs(U))));
-  return fmaxf(__fadd_ru(w, mg), 0.0f);
+// ---- the binary32 screen ---------------------------------------------------
+//
+// For a > 0 the upper-bound candidate of x_j from the right-hand side is, in
+// exact arithmetic, L_j + s/a with s = rhs - minact; it is applied only if
+// it lies below U_j - tau*max(1,|U_j|) (continuous) or, after rounding,
+// below U_j (integer: L_j + s/a < U_j - eps_int).  So it can only be applied
+// if  s < |a| WU_j  with  WU_j = U_j - L_j - tau*max(1,|U_j|)  (continuous)
+// or  U_j - L_j - eps_int  (integer).  The three other sign/side cases give
+// the same form with WL_j (lower candidates use max(1,|L_j|)):
+//   right-hand side: a > 0 -> upper (WU), a < 0 -> lower (WL)
+//   left-hand side:  a > 0 -> lower (WL), a < 0 -> upper (WU)
+// The record stores binary32 upper bounds of WU, WL enlarged by
+// 2^-40 (|L|+|U|), clamped at 0; a row side stores a binary32 lower bound
+// thr of s - 2^-39 (|side| + |activity|).  These margins exceed the rounding
+// of every binary64 operation of the candidate formula and of the
+// acceptance threshold, so  upper(|a|) * W <= thr  proves that the
+// nonzero's candidate from that side is not applied.
+
+__device__ __forceinline__ void screen_widths(double L, double U, bool isint, float tau_dn,
+                                              float eps_dn, float &WU, float &WL) {
+  float base = __fsub_ru(f32_up(U), f32_dn(L));
+  if (!(base <= FLT_MAX)) {  // an infinite (or unrepresentable) width
+    WU = WL = f_inf();
+    return;
+  }
+  float absorb = __fmul_ru(0x1p-40f, __fadd_ru(f32_up(d_abs(L)), f32_up(d_abs(U))));
+  float cu, cl;
+  if (isint) {
+    cu = cl = eps_dn;
+  } else {
+    cu = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn(d_abs(U))));
+    cl = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn(d_abs(L))));
+  }
+  WU = fmaxf(__fadd_ru(__fsub_ru(base, cu), absorb), 0.0f);
+  WL = fmaxf(__fadd_ru(__fsub_ru(base, cl), absorb), 0.0f);
+  if (!(WU == WU)) WU = f_inf();  // never NaN (inf - inf on invalid input)
+  if (!(WL == WL)) WL = f_inf();
 }
 
-__device__ __forceinline__ void ld_rec(const VarRec *p, double &L, double &U,
-                                       float &W, uint32_t &flags) {
+__device__ __forceinline__ void ld_rec(const VarRec *p, double &L, double &U, float &WU,
+                                       float &WL, uint32_t &flags) {
   double d2, d3;
   asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
       : "=d"(L), "=d"(U), "=d"(d2), "=d"(d3)
       : "l"(p));
   long long w = __double_as_longlong(d2);
-  W = __int_as_float((int)(w & 0xFFFFFFFFll));
-  flags = (uint32_t)((unsigned long long)w >> 32);
+  WU = __int_as_float((int)(w & 0xFFFFFFFFll));
+  WL = __int_as_float((int)((unsigned long long)w >> 32));
+  flags = (uint32_t)((unsigned long long)__double_as_longlong(d3) & 0xFFFFFFFFull);
 }
 
-__device__ __forceinline__ void st_rec(VarRec *p, double L, double U, float W,
+__device__ __forceinline__ void st_rec(VarRec *p, double L, double U, float WU, float WL,
                                        uint32_t flags) {
-  long long w = (long long)(((unsigned long long)flags << 32) |
-                            (unsigned long long)__float_as_uint(W));
+  long long w = (long long)(((unsigned long long)__float_as_uint(WL) << 32) |
+                            (unsigned long long)__float_as_uint(WU));
   double d2 = __longlong_as_double(w);
-  double d3 = 0.0;
-  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(L),
-               "d"(U), "d"(d2), "d"(d3)
+  double d3 = __longlong_as_double((long long)flags);
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(L), "d"(U), "d"(d2),
+               "d"(d3)
                : "memory");
+}
+
+__device__ __forceinline__ void write_var(VarRec *p, double L, double U, uint32_t vt,
+                                          float tau_dn, float eps_dn) {
+  float WU, WL;
+  screen_widths(L, U, vt != 0u, tau_dn, eps_dn, WU, WL);
+  st_rec(p, L, U, WU, WL, vt);
 }
 
 __device__ __forceinline__ void set_flag(int32_t *f) {
@@ -130,32 +177,23 @@ __device__ __forceinline__ void set_flag(int32_t *f) {
 
 // ------------------------------------------------------- per-row decisions --
 
-// Everything the candidate step needs to know about one row.
+// What the candidate step needs to know about one row (kept in shared
+// memory so that any lane of the warp can process any lane's nonzeros).
 struct RowView {
   double minfin, maxfin, lhs, rhs;
   int32_t mininf, maxinf;
-  float thr_r, thr_l;  // screen thresholds (see row_sides)
-  bool act;            // some nonzero may produce an accepted candidate
+  float thr_r, thr_l;
+  int32_t exact;
+  int32_t act;  // some nonzero of the row may yield an accepted candidate
 };
 
-// Step 2 of Sec. 1.1 for both sides of a row, and the binary32 screen.
-//
-// Screen (sound, never changes a result): for a > 0 the upper-bound
-// candidate of x_j from the right-hand side is L_j + s/a with slack
-// s = rhs - minact, and it can only be applied if s < a (U_j - L_j); the
-// three other sign/side cases reduce to the same test s < |a| (U_j - L_j)
-// with s the slack of that side.  With W_j >= (U_j-L_j) + 2^-40 (|L_j|+|U_j|)
-// and t = an upper bound on |a| W_j, a side whose slack satisfies
-//    s (1 - 2^-20) - 2^-40 (|side| + |activity|) >= t
-// provably yields no accepted candidate for that nonzero, whatever the
-// rounding of the binary64 formulas.  thr is a binary32 lower bound on the
-// left-hand side; T is the row maximum of t.
-__device__ __forceinline__ void row_sides(RowView &rv, float T, double eps_feas,
+// Step 2 of Sec. 1.1 for both sides of a row, and the screen thresholds.
+__device__ __forceinline__ void row_sides(RowView &rv, float Tr, float Tl, double eps_feas,
                                           int32_t *infeasible_flag) {
   bool infeas = false;
   bool act_r = false, act_l = false;
-  rv.thr_r = __uint_as_float(0x7F800000u);
-  rv.thr_l = __uint_as_float(0x7F800000u);
+  rv.thr_r = f_inf();
+  rv.thr_l = f_inf();
   if (d_isfinite(rv.rhs) && rv.mininf <= 1) {
     if (rv.mininf == 1) {
       act_r = true;  // only the nonzero with the infinite contribution
@@ -165,10 +203,9 @@ __device__ __forceinline__ void row_sides(RowView &rv, float T, double eps_feas,
         double thr = rv.rhs + eps_feas * fmax(1.0, fabs(rv.rhs));
         if (rv.minfin > thr) infeas = true;
       }
-      float sd = f32_dn(s);
-      float mg = __fmul_ru(0x1p-40f, __fadd_ru(f32_up(d_abs(rv.rhs)), f32_up(d_abs(rv.minfin))));
-      rv.thr_r = __fsub_rd(__fmul_rd(sd, 1.0f - 0x1p-20f), mg);
-      act_r = T > rv.thr_r;
+      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up(d_abs(rv.rhs)), f32_up(d_abs(rv.minfin))));
+      rv.thr_r = __fsub_rd(f32_dn(s), mg);
+      act_r = Tr > rv.thr_r;
     }
   }
   if (d_isfinite(rv.lhs) && rv.maxinf <= 1) {
@@ -180,14 +217,30 @@ __device__ __forceinline__ void row_sides(RowView &rv, float T, double eps_feas,
         double thr = rv.lhs - eps_feas * fmax(1.0, fabs(rv.lhs));
         if (rv.maxfin < thr) infeas = true;
       }
-      float sd = f32_dn(s);
-      float mg = __fmul_ru(0x1p-40f, __fadd_ru(f32_up(d_abs(rv.lhs)), f32_up(d_abs(rv.maxfin))));
-      rv.thr_l = __fsub_rd(__fmul_rd(sd, 1.0f - 0x1p-20f), mg);
-      act_l = T > rv.thr_l;
+      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up(d_abs(rv.lhs)), f32_up(d_abs(rv.maxfin))));
+      rv.thr_l = __fsub_rd(f32_dn(s), mg);
+      act_l = Tl > rv.thr_l;
     }
   }
   if (infeas) set_flag(infeasible_flag);
-  rv.act = act_r || act_l;
+  rv.act = (act_r || act_l) ? 1 : 0;
+}
+
+// Which sides of one nonzero survive the screen (bit 0: right-hand side,
+// bit 1: left-hand side).
+__device__ __forceinline__ unsigned nnz_sides(double a, double L, double U, float WU,
+                                              float WL, const RowView &rv) {
+  bool pos = d_pos(a);
+  double bmin = pos ? L : U;
+  double bmax = pos ? U : L;
+  float au = absup_fast(a);
+  float tr = rv.exact ? f_inf() : __fmul_ru(au, pos ? WU : WL);
+  float tl = rv.exact ? f_inf() : __fmul_ru(au, pos ? WL : WU);
+  bool r = d_isfinite(rv.rhs) &&
+           ((rv.mininf == 0 && tr > rv.thr_r) || (rv.mininf == 1 && d_isinf(bmin)));
+  bool l = d_isfinite(rv.lhs) &&
+           ((rv.maxinf == 0 && tl > rv.thr_l) || (rv.maxinf == 1 && d_isinf(bmax)));
+  return (r ? 1u : 0u) | (l ? 2u : 0u);
 }
 
 // Bound candidates of one nonzero (Eq. 3a/3b in the residual form of
@@ -195,32 +248,23 @@ __device__ __forceinline__ void row_sides(RowView &rv, float T, double eps_feas,
 // rounding (Step 3), and the filtered atomic update (Sec. 3.5).  Candidates
 // are compared with the bounds at the start of the round (L, U) and applied
 // to the next state with order-preserving 64-bit atomics.
-__device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L,
-                                               double U, float W,
-                                               uint32_t flags, bool exact,
-                                               const RowView &rv,
-                                               const Ctrl &prm,
-                                               long long *keys,
-                                               int32_t *changed) {
+__device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L, double U,
+                                               uint32_t flags, unsigned sides,
+                                               const RowView &rv, const Ctrl &prm,
+                                               long long *keys, int32_t *changed) {
   bool pos = d_pos(a);
   double bmin = pos ? L : U;
   double bmax = pos ? U : L;
-  float t = exact ? __uint_as_float(0x7F800000u) : __fmul_ru(absup_fast(a), W);
-  bool try_r = d_isfinite(rv.rhs) &&
-               ((rv.mininf == 0 && t > rv.thr_r) || (rv.mininf == 1 && d_isinf(bmin)));
-  bool try_l = d_isfinite(rv.lhs) &&
-               ((rv.maxinf == 0 && t > rv.thr_l) || (rv.maxinf == 1 && d_isinf(bmax)));
-  if (!try_r && !try_l) return;
   double lc = 0.0, uc = 0.0;
   bool hl = false, hu = false;
-  if (try_r) {
+  if (sides & 1u) {
     double res = (rv.mininf == 0) ? fma(-a, bmin, rv.minfin) : rv.minfin;
     if (d_isfinite(res)) {
       double c = (rv.rhs - res) / a;
       if (pos) { uc = c; hu = true; } else { lc = c; hl = true; }
     }
   }
-  if (try_l) {
+  if (sides & 2u) {
     double res = (rv.maxinf == 0) ? fma(-a, bmax, rv.maxfin) : rv.maxfin;
     if (d_isfinite(res)) {
       double c = (rv.lhs - res) / a;
@@ -258,29 +302,170 @@ __device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L,
   }
 }
 
+// Per-warp shared state of the candidate step.
+struct WarpScratch {
+  RowView rows[kSliceW];
+  uint32_t work[2 * kSliceW];
+};
+
+__device__ __forceinline__ void top2_add(float t, int k, float &t1, float &t2, int32_t &k1) {
+  if (t > t1) {
+    t2 = t1;
+    t1 = t;
+    k1 = k;
+  } else if (t > t2) {
+    t2 = t;
+  }
+}
+
+__device__ __forceinline__ Top2 top2_init() {
+  Top2 t;
+  t.r1 = t.r2 = t.l1 = t.l2 = -f_inf();
+  t.kr = t.kl = 0;
+  return t;
+}
+
+// a work-list entry: slot k of lane o, sides to evaluate (bit 0 rhs, bit 1 lhs)
+__device__ __forceinline__ uint32_t pack_entry(int k, unsigned sides, int o) {
+  return ((uint32_t)k << 7) | (sides << 5) | (uint32_t)o;
+}
+
+// Candidate step of one warp over its slice.  A lane with an active chunk
+// contributes the nonzeros that survive the screen to a per-warp work list;
+// the whole warp evaluates the list 32 entries at a time, so the binary64
+// candidate formulas always run lane-dense.  When the second-largest screen
+// value of a chunk is below the threshold, only the chunk's largest can
+// survive and it is listed directly (no re-read); otherwise the lane re-reads
+// its chunk (values and columns from L2, records through the same gather),
+// four slots at a time.  All 32 lanes must call this (warp collectives).
+__device__ __forceinline__ void warp_candidates(const RowView &mine, const Top2 &t,
+                                                int chunk_mininf, int chunk_maxinf,
+                                                int32_t mylen, const double *slice_val,
+                                                const int32_t *slice_col, const VarRec *rec,
+                                                const Ctrl &prm, long long *keys,
+                                                int32_t *changed, WarpScratch &ws) {
+  const int lane = threadIdx.x & 31;
+  const bool act = mine.act != 0;
+  if (__ballot_sync(kFull, act) == 0u) return;
+  ws.rows[lane] = mine;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  int nwork = 0;
+
+  auto process = [&](uint32_t e) {
+    const int o = (int)(e & 31u);
+    const int k = (int)(e >> 7);
+    const unsigned sides = (e >> 5) & 3u;
+    const RowView &rv = ws.rows[o];
+    const int64_t off = (int64_t)k * kSliceW + o;
+    double a = slice_val[off];
+    int32_t j = slice_col[off];
+    double L, U;
+    float WU, WL;
+    uint32_t fl;
+    ld_rec(rec + j, L, U, WU, WL, fl);
+    nnz_candidates(a, j, L, U, fl, sides, rv, prm, keys, changed);
+  };
+  auto append = [&](bool h, uint32_t e) {
+    const unsigned pm = __ballot_sync(kFull, h);
+    if (h) ws.work[nwork + __popc(pm & lt)] = e;
+    nwork += __popc(pm);
+    if (nwork >= kSliceW) {
+      __syncwarp();
+      process(ws.work[lane]);
+      __syncwarp();
+      uint32_t keep = (lane + kSliceW < nwork) ? ws.work[lane + kSliceW] : 0u;
+      __syncwarp();
+      if (lane + kSliceW < nwork) ws.work[lane] = keep;
+      nwork -= kSliceW;
+      __syncwarp();
+    }
+  };
+
+  const bool full = act && (mine.exact || (mine.mininf == 1 && chunk_mininf > 0) ||
+                            (mine.maxinf == 1 && chunk_maxinf > 0) || t.r2 > mine.thr_r ||
+                            t.l2 > mine.thr_l);
+  // only the largest screen value of a side can pass: list it directly
+  bool h1 = false, h2 = false;
+  uint32_t e1 = 0u, e2 = 0u;
+  if (act && !full) {
+    const bool pr = t.r1 > mine.thr_r, pl = t.l1 > mine.thr_l;
+    if (pr && pl && t.kr == t.kl) {
+      h1 = true;
+      e1 = pack_entry(t.kr, 3u, lane);
+    } else {
+      if (pr) { h1 = true; e1 = pack_entry(t.kr, 1u, lane); }
+      if (pl) { h2 = true; e2 = pack_entry(t.kl, 2u, lane); }
+    }
+  }
+  append(h1, e1);
+  append(h2, e2);
+
+  // full re-read of the chunk, four slots at a time
+  const int len = full ? mylen : 0;
+  int maxlen = len;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kFull, maxlen, off));
+  for (int k = 0; k < maxlen; k += 4) {
+    double a[4];
+    int32_t j[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = 1.0;
+      j[u] = 0;
+      if (k + u < len) {
+        const int64_t off = (int64_t)(k + u) * kSliceW + lane;
+        a[u] = slice_val[off];
+        j[u] = slice_col[off];
+      }
+    }
+    unsigned sd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      sd[u] = 0u;
+      if (k + u < len) {
+        double L, U;
+        float WU, WL;
+        uint32_t fl;
+        ld_rec(rec + j[u], L, U, WU, WL, fl);
+        sd[u] = nnz_sides(a[u], L, U, WU, WL, mine);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) append(sd[u] != 0u, pack_entry(k + u, sd[u], lane));
+  }
+  __syncwarp();
+  if (lane < nwork) process(ws.work[lane]);
+  __syncwarp();
+}
+
 // ------------------------------------------------------------- k_round --
 
 constexpr int kRoundWarps = 8;
 
 __global__ void __launch_bounds__(kRoundWarps * 32)
 k_round(DevMatrix M, DevState S) {
+  __shared__ WarpScratch scratch[kRoundWarps];
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
-  const int slice = blockIdx.x * kRoundWarps + (threadIdx.x >> 5);
+  const int wib = threadIdx.x >> 5;
+  const int slice = blockIdx.x * kRoundWarps + wib;
   const int lane = threadIdx.x & 31;
-  if (slice >= M.nslices) return;
+  if (slice >= M.nslices) return;  // warp-uniform
   const int64_t c = (int64_t)slice * kSliceW + lane;
   const int32_t lenf = M.chunk_len[c];
   const int32_t len = lenf & kLenMask;
   const int32_t row = M.chunk_row[c];
-  const int64_t base = M.slice_off[slice] + lane;
-  const double *vp = M.val + base;
-  const int32_t *cp = M.col + base;
+  const int64_t sbase = M.slice_off[slice];
+  const double *svp = M.val + sbase;
+  const int32_t *scp = M.col + sbase;
+  const double *vp = svp + lane;
+  const int32_t *cp = scp + lane;
 
   // ---- activities of the chunk (Def. 1, Eq. 2a/2b; Sec. 3.4) ----
   double minfin = 0.0, maxfin = 0.0;
   int32_t mininf = 0, maxinf = 0;
-  float T = 0.0f;
+  Top2 t = top2_init();
   int k = 0;
   for (; k + 4 <= len; k += 4) {
     double a[4];
@@ -291,10 +476,10 @@ k_round(DevMatrix M, DevState S) {
       j[u] = __ldcs(cp + (int64_t)(k + u) * kSliceW);
     }
     double L[4], U[4];
-    float W[4];
+    float WU[4], WL[4];
     uint32_t fl[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) ld_rec(S.rec + j[u], L[u], U[u], W[u], fl[u]);
+    for (int u = 0; u < 4; ++u) ld_rec(S.rec + j[u], L[u], U[u], WU[u], WL[u], fl[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       bool pos = d_pos(a[u]);
@@ -305,16 +490,18 @@ k_round(DevMatrix M, DevState S) {
       maxinf += imax;
       minfin = fma(a[u], imin ? 0.0 : bmin, minfin);
       maxfin = fma(a[u], imax ? 0.0 : bmax, maxfin);
-      T = fmaxf(T, __fmul_ru(absup_fast(a[u]), W[u]));
+      float au = absup_fast(a[u]);
+      top2_add(__fmul_ru(au, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
+      top2_add(__fmul_ru(au, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
     }
   }
   for (; k < len; ++k) {
     double a = __ldcs(vp + (int64_t)k * kSliceW);
     int32_t j = __ldcs(cp + (int64_t)k * kSliceW);
     double L, U;
-    float W;
+    float WU, WL;
     uint32_t fl;
-    ld_rec(S.rec + j, L, U, W, fl);
+    ld_rec(S.rec + j, L, U, WU, WL, fl);
     bool pos = d_pos(a);
     double bmin = pos ? L : U;
     double bmax = pos ? U : L;
@@ -323,45 +510,47 @@ k_round(DevMatrix M, DevState S) {
     maxinf += imax;
     minfin = fma(a, imin ? 0.0 : bmin, minfin);
     maxfin = fma(a, imax ? 0.0 : bmax, maxfin);
-    T = fmaxf(T, __fmul_ru(absup_fast(a), W));
+    float au = absup_fast(a);
+    top2_add(__fmul_ru(au, pos ? WU : WL), k, t.r1, t.r2, t.kr);
+    top2_add(__fmul_ru(au, pos ? WL : WU), k, t.l1, t.l2, t.kl);
   }
-  if (row < 0) return;  // padding lane
   const bool exact = (lenf & kExactFlag) != 0;
-  if (exact) T = __uint_as_float(0x7F800000u);
+  if (exact) t.r1 = t.r2 = t.l1 = t.l2 = f_inf();
 
-  if (c < (int64_t)M.nslices_split * kSliceW) {
-    // chunk of a split row: hand the partial sums to k_combine
-    Partial p;
-    p.minfin = minfin;
-    p.maxfin = maxfin;
-    p.mininf = mininf;
-    p.maxinf = maxinf;
-    p.T = T;
-    p.exact = exact ? 1 : 0;
-    S.part[c] = p;
+  if (slice < M.nslices_split) {  // warp-uniform: split chunks only
+    if (row >= 0) {
+      Partial p;
+      p.minfin = minfin;
+      p.maxfin = maxfin;
+      p.mininf = mininf;
+      p.maxinf = maxinf;
+      p.t = t;
+      p.exact = exact ? 1 : 0;
+      p.pad = 0;
+      S.part[c] = p;
+    }
     return;
   }
 
-  // ---- whole row: Step 2, screen, candidates ----
+  // ---- whole rows: Step 2, screen, candidates ----
   RowView rv;
   rv.minfin = minfin;
   rv.maxfin = maxfin;
   rv.mininf = mininf;
   rv.maxinf = maxinf;
-  rv.lhs = S.lhs[row];
-  rv.rhs = S.rhs[row];
-  Ctrl prm = *ctrl;
-  row_sides(rv, T, prm.eps_feas, &S.ctrl->infeasible);
-  if (!rv.act) return;
-  for (int q = 0; q < len; ++q) {
-    double a = vp[(int64_t)q * kSliceW];
-    int32_t j = cp[(int64_t)q * kSliceW];
-    double L, U;
-    float W;
-    uint32_t fl;
-    ld_rec(S.rec + j, L, U, W, fl);
-    nnz_candidates(a, j, L, U, W, fl, exact, rv, prm, S.keys, &S.ctrl->changed);
+  rv.exact = exact ? 1 : 0;
+  rv.act = 0;
+  rv.thr_r = rv.thr_l = f_inf();
+  if (row >= 0) {
+    rv.lhs = S.lhs[row];
+    rv.rhs = S.rhs[row];
+    row_sides(rv, t.r1, t.l1, ctrl->eps_feas, &S.ctrl->infeasible);
+  } else {
+    rv.lhs = rv.rhs = 0.0;
   }
+  const Ctrl prm = *ctrl;
+  warp_candidates(rv, t, mininf, maxinf, len, svp, scp, S.rec, prm, S.keys, &S.ctrl->changed,
+                  scratch[wib]);
 }
 
 // ------------------------------------------------------------ k_combine --
@@ -378,26 +567,28 @@ k_combine(DevMatrix M, DevState S) {
   const int32_t cb = M.split_cbeg[w], ce = M.split_cbeg[w + 1];
   double mnf = 0.0, mxf = 0.0;
   int32_t mni = 0, mxi = 0, ex = 0;
-  float T = 0.0f;
+  float Tr = -f_inf(), Tl = -f_inf();
   for (int32_t c = cb + lane; c < ce; c += kSliceW) {
     Partial p = S.part[c];
     mnf += p.minfin;
     mxf += p.maxfin;
     mni += p.mininf;
     mxi += p.maxinf;
-    T = fmaxf(T, p.T);
+    Tr = fmaxf(Tr, p.t.r1);
+    Tl = fmaxf(Tl, p.t.l1);
     ex |= p.exact;
   }
   // butterfly reduction: a fixed pattern, so the sum is reproducible and
   // identical in every lane (binary64 addition is commutative)
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    mnf += __shfl_xor_sync(0xFFFFFFFFu, mnf, off);
-    mxf += __shfl_xor_sync(0xFFFFFFFFu, mxf, off);
-    mni += __shfl_xor_sync(0xFFFFFFFFu, mni, off);
-    mxi += __shfl_xor_sync(0xFFFFFFFFu, mxi, off);
-    T = fmaxf(T, __shfl_xor_sync(0xFFFFFFFFu, T, off));
-    ex |= __shfl_xor_sync(0xFFFFFFFFu, ex, off);
+    mnf += __shfl_xor_sync(kFull, mnf, off);
+    mxf += __shfl_xor_sync(kFull, mxf, off);
+    mni += __shfl_xor_sync(kFull, mni, off);
+    mxi += __shfl_xor_sync(kFull, mxi, off);
+    Tr = fmaxf(Tr, __shfl_xor_sync(kFull, Tr, off));
+    Tl = fmaxf(Tl, __shfl_xor_sync(kFull, Tl, off));
+    ex |= __shfl_xor_sync(kFull, ex, off);
   }
   if (lane != 0) return;
   const int32_t row = M.split_row[w];
@@ -408,8 +599,9 @@ k_combine(DevMatrix M, DevState S) {
   rv.maxinf = mxi;
   rv.lhs = S.lhs[row];
   rv.rhs = S.rhs[row];
-  if (ex) T = __uint_as_float(0x7F800000u);
-  row_sides(rv, T, ctrl->eps_feas, &S.ctrl->infeasible);
+  rv.exact = ex;
+  if (ex) Tr = Tl = f_inf();
+  row_sides(rv, Tr, Tl, ctrl->eps_feas, &S.ctrl->infeasible);
   RowTot rt;
   rt.minfin = mnf;
   rt.maxfin = mxf;
@@ -417,7 +609,7 @@ k_combine(DevMatrix M, DevState S) {
   rt.maxinf = mxi;
   rt.thr_r = rv.thr_r;
   rt.thr_l = rv.thr_l;
-  rt.active = rv.act ? 1 : 0;
+  rt.active = rv.act;
   rt.row = row;
   S.rowtot[w] = rt;
 }
@@ -426,40 +618,48 @@ k_combine(DevMatrix M, DevState S) {
 
 __global__ void __launch_bounds__(kRoundWarps * 32)
 k_cand_split(DevMatrix M, DevState S) {
+  __shared__ WarpScratch scratch[kRoundWarps];
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
-  const int slice = blockIdx.x * kRoundWarps + (threadIdx.x >> 5);
+  const int wib = threadIdx.x >> 5;
+  const int slice = blockIdx.x * kRoundWarps + wib;
   const int lane = threadIdx.x & 31;
-  if (slice >= M.nslices_split) return;
+  if (slice >= M.nslices_split) return;  // warp-uniform
   const int64_t c = (int64_t)slice * kSliceW + lane;
   const int32_t sidx = M.chunk_sidx[c];
-  if (sidx < 0) return;
-  const RowTot rt = S.rowtot[sidx];
-  if (!rt.active) return;
-  const int32_t lenf = M.chunk_len[c];
-  const int32_t len = lenf & kLenMask;
-  const bool exact = (lenf & kExactFlag) != 0;
-  const int64_t base = M.slice_off[slice] + lane;
   RowView rv;
-  rv.minfin = rt.minfin;
-  rv.maxfin = rt.maxfin;
-  rv.mininf = rt.mininf;
-  rv.maxinf = rt.maxinf;
-  rv.thr_r = rt.thr_r;
-  rv.thr_l = rt.thr_l;
-  rv.lhs = S.lhs[rt.row];
-  rv.rhs = S.rhs[rt.row];
-  rv.act = true;
-  Ctrl prm = *ctrl;
-  for (int q = 0; q < len; ++q) {
-    double a = M.val[base + (int64_t)q * kSliceW];
-    int32_t j = M.col[base + (int64_t)q * kSliceW];
-    double L, U;
-    float W;
-    uint32_t fl;
-    ld_rec(S.rec + j, L, U, W, fl);
-    nnz_candidates(a, j, L, U, W, fl, exact, rv, prm, S.keys, &S.ctrl->changed);
+  rv.act = 0;
+  rv.exact = 0;
+  rv.mininf = rv.maxinf = 0;
+  rv.minfin = rv.maxfin = rv.lhs = rv.rhs = 0.0;
+  rv.thr_r = rv.thr_l = f_inf();
+  Top2 t = top2_init();
+  int32_t len = 0, cmin = 0, cmax = 0;
+  if (sidx >= 0) {
+    const RowTot rt = S.rowtot[sidx];
+    if (rt.active) {
+      const Partial p = S.part[c];
+      const int32_t lenf = M.chunk_len[c];
+      len = lenf & kLenMask;
+      rv.minfin = rt.minfin;
+      rv.maxfin = rt.maxfin;
+      rv.mininf = rt.mininf;
+      rv.maxinf = rt.maxinf;
+      rv.thr_r = rt.thr_r;
+      rv.thr_l = rt.thr_l;
+      rv.lhs = S.lhs[rt.row];
+      rv.rhs = S.rhs[rt.row];
+      rv.exact = (lenf & kExactFlag) ? 1 : 0;
+      rv.act = 1;
+      t = p.t;
+      cmin = p.mininf;
+      cmax = p.maxinf;
+    }
   }
+  const int64_t sbase = M.slice_off[slice];
+  const Ctrl prm = *ctrl;
+  warp_candidates(rv, t, cmin, cmax, len, M.val + sbase, M.col + sbase, S.rec, prm, S.keys,
+                  &S.ctrl->changed, scratch[wib]);
 }
 
 // ------------------------------------------------------------- k_finish --
@@ -470,11 +670,12 @@ constexpr int kFinishThreads = 256;
 // arrive (threadfence-reduction pattern; nobody waits) counts the round and
 // sets the WHILE condition of the enclosing graph node.
 __global__ void __launch_bounds__(kFinishThreads)
-k_finish(DevState S, const uint8_t *vartype, int32_t n,
-         cudaGraphConditionalHandle handle) {
+k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHandle handle,
+         int use_cond) {
   Ctrl *ctrl = S.ctrl;
   const int32_t err = ctrl->err;
   const double eps_feas = ctrl->eps_feas;
+  const float tau_dn = f32_dn(ctrl->tau_rel), eps_dn = f32_dn(ctrl->eps_int);
   if (!err) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -485,7 +686,7 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n,
         bool cross = vt ? (L > U) : (L > U + eps_feas * fmax(1.0, fabs(U)));
         if (cross) set_flag(&ctrl->infeasible);
       }
-      st_rec(S.rec + j, L, U, width_up(L, U), vt);
+      write_var(S.rec + j, L, U, vt, tau_dn, eps_dn);
     }
   }
   __syncthreads();
@@ -503,7 +704,7 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n,
       vc->changed = 0;
       vc->blocks_done = 0;
       __threadfence();
-      cudaGraphSetConditional(handle, (unsigned)cont);
+      if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
     }
   }
 }
@@ -514,9 +715,11 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n,
 // becomes +-inf; integer bounds are rounded (ceil(lb - eps_int),
 // floor(ub + eps_int)); NaN and contradictory infinities set ctrl->err.
 __global__ void k_prologue(DevState S, uint8_t *vt_ws, int32_t m, int32_t n,
-                           const double *lb, const double *ub,
-                           const uint8_t *vartype, const double *lhs,
-                           const double *rhs, double eps_int, double thr) {
+                           const double *lb, const double *ub, const uint8_t *vartype,
+                           const double *lhs, const double *rhs, double eps_int,
+                           double tau_rel, double thr) {
+  const float tau_dn = f32_dn(tau_rel), eps_dn = f32_dn(eps_int);
+  const double pinf = __longlong_as_double(0x7FF0000000000000ll);
   int64_t total = (int64_t)(n > m ? n : m);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -529,14 +732,14 @@ __global__ void k_prologue(DevState S, uint8_t *vt_ws, int32_t m, int32_t n,
         L = 0.0;
         U = 0.0;
       }
-      if (L <= -thr) L = -__longlong_as_double(0x7FF0000000000000ll);
-      if (U >= thr) U = __longlong_as_double(0x7FF0000000000000ll);
+      if (L <= -thr) L = -pinf;
+      if (U >= thr) U = pinf;
       if (vt) {
         if (d_isfinite(L)) L = ceil(L - eps_int);
         if (d_isfinite(U)) U = floor(U + eps_int);
       }
       reinterpret_cast<longlong2 *>(S.keys)[i] = make_longlong2(key_of(L), key_of(U));
-      st_rec(S.rec + i, L, U, width_up(L, U), vt);
+      write_var(S.rec + i, L, U, vt, tau_dn, eps_dn);
       vt_ws[i] = vt;
     }
     if (i < m) {
@@ -547,16 +750,15 @@ __global__ void k_prologue(DevState S, uint8_t *vt_ws, int32_t m, int32_t n,
         l = 0.0;
         r = 0.0;
       }
-      if (l <= -thr) l = -__longlong_as_double(0x7FF0000000000000ll);
-      if (r >= thr) r = __longlong_as_double(0x7FF0000000000000ll);
+      if (l <= -thr) l = -pinf;
+      if (r >= thr) r = pinf;
       S.lhs[i] = l;
       S.rhs[i] = r;
     }
   }
 }
 
-__global__ void k_epilogue(DevState S, int32_t n, double *lb_out,
-                           double *ub_out) {
+__global__ void k_epilogue(DevState S, int32_t n, double *lb_out, double *ub_out) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     longlong2 kk = reinterpret_cast<const longlong2 *>(S.keys)[j];
@@ -574,47 +776,58 @@ static int grid_for(int64_t work, int threads, int max_blocks) {
   return (int)b;
 }
 
-cudaError_t launch_prologue(const DevState &S, uint8_t *vt_ws, int32_t m,
-                            int32_t n, const double *lb, const double *ub,
-                            const uint8_t *vartype, const double *lhs,
-                            const double *rhs, double eps_int, double thr,
-                            int num_sms, cudaStream_t st) {
+cudaError_t launch_prologue(const DevState &S, uint8_t *vt_ws, int32_t m, int32_t n,
+                            const double *lb, const double *ub, const uint8_t *vartype,
+                            const double *lhs, const double *rhs, double eps_int,
+                            double tau_rel, double thr, int num_sms, cudaStream_t st) {
   int64_t total = n > m ? n : m;
   k_prologue<<<grid_for(total, 256, num_sms * 16), 256, 0, st>>>(
-      S, vt_ws, m, n, lb, ub, vartype, lhs, rhs, eps_int, thr);
+      S, vt_ws, m, n, lb, ub, vartype, lhs, rhs, eps_int, tau_rel, thr);
   return cudaGetLastError();
 }
 
-cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out,
-                            double *ub_out, int num_sms, cudaStream_t st) {
+cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out, double *ub_out,
+                            int num_sms, cudaStream_t st) {
   k_epilogue<<<grid_for(n, 256, num_sms * 16), 256, 0, st>>>(S, n, lb_out, ub_out);
   return cudaGetLastError();
 }
 
-// Launches one round's kernels on `st` (called while `st` captures the body
-// of the graph's WHILE node).
-cudaError_t launch_round_body(const DevMatrix &M, const DevState &S,
-                              const uint8_t *vt_ws,
-                              cudaGraphConditionalHandle handle, int num_sms,
-                              cudaStream_t st) {
+// Launches one round's kernels on `st`.  In the graph body (use_cond = 1)
+// k_finish sets the WHILE condition; in the host-driven loop it does not.
+// With `ev` (8 events) each kernel is bracketed by a pair of events.
+cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
+                                 cudaGraphConditionalHandle handle, int use_cond, int num_sms,
+                                 cudaStream_t st, cudaEvent_t *ev) {
+  cudaError_t e;
   int nb = (M.nslices + kRoundWarps - 1) / kRoundWarps;
   if (nb < 1) nb = 1;
+  if (ev) cudaEventRecord(ev[0], st);
   k_round<<<nb, kRoundWarps * 32, 0, st>>>(M, S);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[1], st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (M.nsplit_rows > 0) {
     int nbc = (M.nsplit_rows + kCombineWarps - 1) / kCombineWarps;
+    if (ev) cudaEventRecord(ev[2], st);
     k_combine<<<nbc, kCombineWarps * 32, 0, st>>>(M, S);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int nbs = (M.nslices_split + kRoundWarps - 1) / kRoundWarps;
+    if (ev) cudaEventRecord(ev[4], st);
     k_cand_split<<<nbs, kRoundWarps * 32, 0, st>>>(M, S);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[5], st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   int nbf = grid_for(M.n, kFinishThreads, num_sms * 8);
-  k_finish<<<nbf, kFinishThreads, 0, st>>>(S, vt_ws, M.n, handle);
+  if (ev) cudaEventRecord(ev[6], st);
+  k_finish<<<nbf, kFinishThreads, 0, st>>>(S, vt_ws, M.n, handle, use_cond);
+  if (ev) cudaEventRecord(ev[7], st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_round_body(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
+                              cudaGraphConditionalHandle handle, int num_sms,
+                              cudaStream_t st) {
+  return launch_round_kernels(M, S, vt_ws, handle, 1, num_sms, st, nullptr);
 }
 
 }  // namespace dp

@@ -12,8 +12,8 @@ namespace dp {
 cudaError_t launch_prologue(const DevState &S, uint8_t *vt_ws, int32_t m,
                             int32_t n, const double *lb, const double *ub,
                             const uint8_t *vartype, const double *lhs,
-                            const double *rhs, double eps_int, double thr,
-                            int num_sms, cudaStream_t st);
+                            const double *rhs, double eps_int, double tau_rel,
+                            double thr, int num_sms, cudaStream_t st);
 
 cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out,
                             double *ub_out, int num_sms, cudaStream_t st);
@@ -22,6 +22,12 @@ cudaError_t launch_round_body(const DevMatrix &M, const DevState &S,
                               const uint8_t *vt_ws,
                               cudaGraphConditionalHandle handle, int num_sms,
                               cudaStream_t st);
+
+cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S,
+                                 const uint8_t *vt_ws,
+                                 cudaGraphConditionalHandle handle,
+                                 int use_cond, int num_sms, cudaStream_t st,
+                                 cudaEvent_t *ev);
 
 // Host image of the device layout described in dp_internal.h.
 struct HostLayout {
