@@ -159,11 +159,12 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
  * of Sec. 3.7, which the paper uses for its main results).  Results are
  * identical to dp_propagate; it exists to measure the cost of the host
  * round trip and to time the round's kernels one by one.
- * kernel_ms (nullable, 4 floats): total milliseconds, measured with CUDA
- *   events on the context's stream around each launch, of the four round
- *   kernels in this order: activities + candidates of whole rows, combine of
- *   split rows, candidates of split rows, per-variable finish.
- * kernel_launches (nullable, 4 int32): how many times each was launched.
+ * kernel_ms (nullable, 5 floats): total milliseconds, measured with CUDA
+ *   events on the context's stream around each launch, of the five round
+ *   kernels in this order: activities and screen of every chunk (whole rows
+ *   also queue their candidates), combine of split rows, screen of split
+ *   rows' chunks, evaluation of the queued candidates, per-variable finish.
+ * kernel_launches (nullable, 5 int32): how many times each was launched.
  * Arguments and return values are otherwise those of dp_propagate.
  */
 int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *mat, const double *lb,

@@ -206,7 +206,7 @@ class Result:
     kernel_launches: tuple | None = None  # host loop only: per-kernel counts
 
 
-KERNELS = ("round", "combine", "cand_split", "finish")
+KERNELS = ("round", "combine", "cand_split", "cand_queue", "finish")
 
 
 def _like(x, n):
@@ -243,11 +243,12 @@ def dp_propagate_hostloop(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
     if ub_out is None:
         ub_out = _like(lb, n)
     inf, rounds = C.c_int32(), C.c_int32()
-    ms = (C.c_float * 4)()
-    cnt = (C.c_int32 * 4)()
+    ms = (C.c_float * len(KERNELS))()
+    cnt = (C.c_int32 * len(KERNELS))()
     rc = _check(lib().dp_propagate_hostloop(
         ctx.handle, mat.handle, _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs), _ptr(rhs),
         C.byref(params) if params is not None else None, _ptr(lb_out), _ptr(ub_out),
         C.byref(inf), C.byref(rounds), ms if timing else None, cnt), "dp_propagate_hostloop")
     return Result(lb_out, ub_out, inf.value, rounds.value, rc,
                   tuple(ms) if timing else None, tuple(cnt))
+

@@ -257,6 +257,7 @@ int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
   TRY(upload(mat, H.chunk_sidx, &M.chunk_sidx, st));
   TRY(upload(mat, H.split_row, &M.split_row, st));
   TRY(upload(mat, H.split_cbeg, &M.split_cbeg, st));
+  TRY(upload(mat, H.split_cidx, &M.split_cidx, st));
   dp::DevState &S = mat->S;
   TRY(dev_alloc(mat, &S.rec, (size_t)n));
   TRY(dev_alloc(mat, &S.keys, 2 * (size_t)n));
@@ -264,6 +265,16 @@ int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
   TRY(dev_alloc(mat, &S.rhs, (size_t)m));
   TRY(dev_alloc(mat, &S.part, (size_t)H.nslices_split * dp::kSliceW));
   TRY(dev_alloc(mat, &S.rowtot, (size_t)H.nsplit_rows));
+  {
+    // candidate queue: a quarter of the slots (at least 1M entries) covers the
+    // survivors of the screen on the workloads measured; a full queue falls
+    // back to in-lane evaluation
+    int64_t cap = mat->padded / 4;
+    if (cap < (int64_t(1) << 20)) cap = int64_t(1) << 20;
+    if (cap > mat->padded) cap = mat->padded > 0 ? mat->padded : 1;
+    S.qcap = (int32_t)cap;
+    TRY(dev_alloc(mat, &S.queue, (size_t)cap));
+  }
   TRY(dev_alloc(mat, &S.ctrl, 1));
   TRY(dev_alloc(mat, &mat->vt_ws, (size_t)n));
   TRY(dev_alloc(mat, &mat->st_lb, (size_t)n));
@@ -406,17 +417,19 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
   if (rc) return rc;
   cudaStream_t st = ctx->stream;
   const bool timed = kernel_ms != nullptr;
-  cudaEvent_t ev[8] = {};
+  constexpr int kK = 5;             // kernels of a round, in the documented order
+  const int ev_of[kK] = {0, 2, 4, 8, 6};  // event pair of each (see launch_round_kernels)
+  cudaEvent_t ev[10] = {};
   if (timed) {
-    for (int i = 0; i < 4; ++i) kernel_ms[i] = 0.0f;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < kK; ++i) kernel_ms[i] = 0.0f;
+    for (int i = 0; i < 10; ++i)
       if (cudaEventCreate(&ev[i]) != cudaSuccess) {
         for (int q = 0; q < i; ++q) cudaEventDestroy(ev[q]);
         return DP_ERR_CUDA;
       }
   }
   if (kernel_launches)
-    for (int i = 0; i < 4; ++i) kernel_launches[i] = 0;
+    for (int i = 0; i < kK; ++i) kernel_launches[i] = 0;
   dp::Ctrl *hc = ctx->h_ctrl;
   int status = DP_OK;
   for (int32_t r = 0; r < p.max_rounds; ++r) {
@@ -426,23 +439,18 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { status = DP_ERR_CUDA; break; }
     const bool split = mat->M.nsplit_rows > 0;
-    if (kernel_launches) {
-      kernel_launches[0] += 1;
-      kernel_launches[1] += split;
-      kernel_launches[2] += split;
-      kernel_launches[3] += 1;
-    }
-    if (timed) {
+    const bool launched[kK] = {true, split, split, true, true};
+    for (int k = 0; k < kK; ++k) {
+      if (!launched[k]) continue;
+      if (kernel_launches) kernel_launches[k] += 1;
       float t;
-      for (int k = 0; k < 4; ++k) {
-        if ((k == 1 || k == 2) && !split) continue;
-        if (cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) kernel_ms[k] += t;
-      }
+      if (timed && cudaEventElapsedTime(&t, ev[ev_of[k]], ev[ev_of[k] + 1]) == cudaSuccess)
+        kernel_ms[k] += t;
     }
     if (hc->err || !hc->last_changed || hc->infeasible) break;
   }
   if (timed)
-    for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 10; ++i) cudaEventDestroy(ev[i]);
   if (status) return status;
   return end_call(ctx, mat, p, lb_out, ub_out, infeasible, rounds);
 }

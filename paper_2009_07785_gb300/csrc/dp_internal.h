@@ -3,7 +3,7 @@
 // Device layout of a loaded matrix ("sliced ELL over row chunks"):
 //   Every row is cut into chunks of at most `chunk` nonzeros (a row that
 //   fits is one chunk).  Chunks of rows that had to be split ("split rows")
-//   come first, grouped by row; the remaining single-chunk rows follow,
+//   come first, sorted by length; the remaining single-chunk rows follow,
 //   sorted by length, longest first.  32 consecutive chunks form a slice,
 //   which one warp processes with one chunk per lane.  A slice stores its
 //   nonzeros slot-major: element (slot k, lane t) of slice s sits at
@@ -54,6 +54,15 @@ struct alignas(16) RowTot {
   int32_t row;
 };
 
+// One nonzero whose candidates survived the screen, with its row's sums,
+// queued for the lane-dense candidate kernel.
+struct alignas(16) CandEntry {
+  double minfin, maxfin, lhs, rhs;
+  int32_t mininf, maxinf;
+  int32_t off;     // element offset of the nonzero in val/col
+  uint32_t sides;  // bit 0: right-hand side, bit 1: left-hand side
+};
+
 // Device control block of one propagation run.
 struct Ctrl {
   int32_t round;        // executed rounds
@@ -63,7 +72,7 @@ struct Ctrl {
   int32_t infeasible;
   int32_t err;          // 0, or a DP_ERR_* code found by the prologue
   uint32_t blocks_done; // arrival counter of the last kernel of a round
-  int32_t pad;
+  int32_t qcount;       // entries appended to the candidate queue this round
   double eps_int, tau_rel, eps_feas, inf_thr;
 };
 
@@ -82,10 +91,14 @@ struct DevMatrix {
   const int32_t *chunk_len; // [nslices*32] length | kExactFlag
   const int32_t *chunk_sidx;// [nslices_split*32] split-row index, -1 = none
   const int32_t *split_row; // [nsplit_rows] row id of each split row
-  const int32_t *split_cbeg;// [nsplit_rows+1] chunk-slot range of each split row
+  const int32_t *split_cbeg;// [nsplit_rows+1] range of each split row in split_cidx
+  const int32_t *split_cidx;// chunk slots of the split rows' pieces, row by row
 };
 
 struct DevState {
+  CandEntry *queue;     // [qcap] candidate queue
+  int32_t qcap;
+  int32_t pad;
   VarRec *rec;          // [n] state at the start of the round
   long long *keys;      // [2n] next state as order-preserving int64 keys
   double *lhs, *rhs;    // [m] normalised sides

@@ -199,7 +199,7 @@ __device__ __forceinline__ void row_sides(RowView &rv, float Tr, float Tl, doubl
       act_r = true;  // only the nonzero with the infinite contribution
     } else {
       double s = rv.rhs - rv.minfin;
-      if (s < 0.0) {
+      if (__double2hiint(s) < 0) {  // s < 0 (or -0, harmless)
         double thr = rv.rhs + eps_feas * fmax(1.0, fabs(rv.rhs));
         if (rv.minfin > thr) infeas = true;
       }
@@ -213,7 +213,7 @@ __device__ __forceinline__ void row_sides(RowView &rv, float Tr, float Tl, doubl
       act_l = true;
     } else {
       double s = rv.maxfin - rv.lhs;
-      if (s < 0.0) {
+      if (__double2hiint(s) < 0) {
         double thr = rv.lhs - eps_feas * fmax(1.0, fabs(rv.lhs));
         if (rv.maxfin < thr) infeas = true;
       }
@@ -302,12 +302,6 @@ __device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L, do
   }
 }
 
-// Per-warp shared state of the candidate step.
-struct WarpScratch {
-  RowView rows[kSliceW];
-  uint32_t work[2 * kSliceW];
-};
-
 __device__ __forceinline__ void top2_add(float t, int k, float &t1, float &t2, int32_t &k1) {
   if (t > t1) {
     t2 = t1;
@@ -325,87 +319,86 @@ __device__ __forceinline__ Top2 top2_init() {
   return t;
 }
 
-// a work-list entry: slot k of lane o, sides to evaluate (bit 0 rhs, bit 1 lhs)
-__device__ __forceinline__ uint32_t pack_entry(int k, unsigned sides, int o) {
-  return ((uint32_t)k << 7) | (sides << 5) | (uint32_t)o;
-}
-
-// Candidate step of one warp over its slice.  A lane with an active chunk
-// contributes the nonzeros that survive the screen to a per-warp work list;
-// the whole warp evaluates the list 32 entries at a time, so the binary64
-// candidate formulas always run lane-dense.  When the second-largest screen
-// value of a chunk is below the threshold, only the chunk's largest can
-// survive and it is listed directly (no re-read); otherwise the lane re-reads
-// its chunk (values and columns from L2, records through the same gather),
-// four slots at a time.  All 32 lanes must call this (warp collectives).
-__device__ __forceinline__ void warp_candidates(const RowView &mine, const Top2 &t,
-                                                int chunk_mininf, int chunk_maxinf,
-                                                int32_t mylen, const double *slice_val,
-                                                const int32_t *slice_col, const VarRec *rec,
-                                                const Ctrl &prm, long long *keys,
-                                                int32_t *changed, WarpScratch &ws) {
+// Queues nonzeros of the lanes' chunks whose candidates survive the screen.
+// Entries go to a global queue (warp-aggregated slots) and are evaluated by
+// k_cand_queue, one per thread, so the binary64 candidate formulas run
+// lane-dense across the whole GPU however few survivors a warp has.  When
+// the second-largest screen value of a side is below the threshold, only the
+// chunk's largest can survive and it is queued directly (no re-read);
+// otherwise the lane re-reads its chunk (values and columns from L2, records
+// through the same gather), four slots at a time.  If the queue is full the
+// lane evaluates the nonzero itself (same result, divergent).  All 32 lanes
+// must call this (warp collectives).
+__device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t, int chunk_mininf,
+                                             int chunk_maxinf, int32_t mylen,
+                                             int64_t slice_off_elems, const double *val,
+                                             const int32_t *col, const DevState &S,
+                                             const Ctrl &prm) {
   const int lane = threadIdx.x & 31;
   const bool act = mine.act != 0;
   if (__ballot_sync(kFull, act) == 0u) return;
-  ws.rows[lane] = mine;
-  __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
-  int nwork = 0;
 
-  auto process = [&](uint32_t e) {
-    const int o = (int)(e & 31u);
-    const int k = (int)(e >> 7);
-    const unsigned sides = (e >> 5) & 3u;
-    const RowView &rv = ws.rows[o];
-    const int64_t off = (int64_t)k * kSliceW + o;
-    double a = slice_val[off];
-    int32_t j = slice_col[off];
-    double L, U;
-    float WU, WL;
-    uint32_t fl;
-    ld_rec(rec + j, L, U, WU, WL, fl);
-    nnz_candidates(a, j, L, U, fl, sides, rv, prm, keys, changed);
-  };
-  auto append = [&](bool h, uint32_t e) {
+  auto push = [&](bool h, int k, unsigned sides) {
     const unsigned pm = __ballot_sync(kFull, h);
-    if (h) ws.work[nwork + __popc(pm & lt)] = e;
-    nwork += __popc(pm);
-    if (nwork >= kSliceW) {
-      __syncwarp();
-      process(ws.work[lane]);
-      __syncwarp();
-      uint32_t keep = (lane + kSliceW < nwork) ? ws.work[lane + kSliceW] : 0u;
-      __syncwarp();
-      if (lane + kSliceW < nwork) ws.work[lane] = keep;
-      nwork -= kSliceW;
-      __syncwarp();
+    if (pm == 0u) return;
+    const int leader = __ffs(pm) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&S.ctrl->qcount, __popc(pm));
+    base = __shfl_sync(kFull, base, leader);
+    if (!h) return;
+    const int slot = base + __popc(pm & lt);
+    const int64_t off = slice_off_elems + (int64_t)k * kSliceW + lane;
+    if (slot < S.qcap) {
+      CandEntry e;
+      e.minfin = mine.minfin;
+      e.maxfin = mine.maxfin;
+      e.lhs = mine.lhs;
+      e.rhs = mine.rhs;
+      e.mininf = mine.mininf;
+      e.maxinf = mine.maxinf;
+      e.off = (int32_t)off;
+      e.sides = sides;
+      S.queue[slot] = e;
+    } else {
+      double a = val[off];
+      int32_t j = col[off];
+      double L, U;
+      float WU, WL;
+      uint32_t fl;
+      ld_rec(S.rec + j, L, U, WU, WL, fl);
+      nnz_candidates(a, j, L, U, fl, sides, mine, prm, S.keys, &S.ctrl->changed);
     }
   };
 
   const bool full = act && (mine.exact || (mine.mininf == 1 && chunk_mininf > 0) ||
                             (mine.maxinf == 1 && chunk_maxinf > 0) || t.r2 > mine.thr_r ||
                             t.l2 > mine.thr_l);
-  // only the largest screen value of a side can pass: list it directly
+  // only the largest screen value of a side can pass: queue it directly
   bool h1 = false, h2 = false;
-  uint32_t e1 = 0u, e2 = 0u;
+  int k1 = 0, k2 = 0;
+  unsigned s1 = 0u;
   if (act && !full) {
     const bool pr = t.r1 > mine.thr_r, pl = t.l1 > mine.thr_l;
     if (pr && pl && t.kr == t.kl) {
       h1 = true;
-      e1 = pack_entry(t.kr, 3u, lane);
+      k1 = t.kr;
+      s1 = 3u;
     } else {
-      if (pr) { h1 = true; e1 = pack_entry(t.kr, 1u, lane); }
-      if (pl) { h2 = true; e2 = pack_entry(t.kl, 2u, lane); }
+      if (pr) { h1 = true; k1 = t.kr; s1 = 1u; }
+      if (pl) { h2 = true; k2 = t.kl; }
     }
   }
-  append(h1, e1);
-  append(h2, e2);
+  push(h1, k1, s1);
+  push(h2, k2, 2u);
 
   // full re-read of the chunk, four slots at a time
   const int len = full ? mylen : 0;
   int maxlen = len;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kFull, maxlen, off));
+  for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kFull, maxlen, o));
+  const double *vp = val + slice_off_elems + lane;
+  const int32_t *cp = col + slice_off_elems + lane;
   for (int k = 0; k < maxlen; k += 4) {
     double a[4];
     int32_t j[4];
@@ -414,9 +407,8 @@ __device__ __forceinline__ void warp_candidates(const RowView &mine, const Top2 
       a[u] = 1.0;
       j[u] = 0;
       if (k + u < len) {
-        const int64_t off = (int64_t)(k + u) * kSliceW + lane;
-        a[u] = slice_val[off];
-        j[u] = slice_col[off];
+        a[u] = vp[(int64_t)(k + u) * kSliceW];
+        j[u] = cp[(int64_t)(k + u) * kSliceW];
       }
     }
     unsigned sd[4];
@@ -427,16 +419,43 @@ __device__ __forceinline__ void warp_candidates(const RowView &mine, const Top2 
         double L, U;
         float WU, WL;
         uint32_t fl;
-        ld_rec(rec + j[u], L, U, WU, WL, fl);
+        ld_rec(S.rec + j[u], L, U, WU, WL, fl);
         sd[u] = nnz_sides(a[u], L, U, WU, WL, mine);
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) append(sd[u] != 0u, pack_entry(k + u, sd[u], lane));
+    for (int u = 0; u < 4; ++u) push(sd[u] != 0u, k + u, sd[u]);
   }
-  __syncwarp();
-  if (lane < nwork) process(ws.work[lane]);
-  __syncwarp();
+}
+
+// ---------------------------------------------------------- k_cand_queue --
+
+// Evaluates the queued nonzeros, one per thread (grid-stride).
+__global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
+  const Ctrl *ctrl = S.ctrl;
+  if (ctrl->err) return;
+  const int32_t cnt = min(ctrl->qcount, S.qcap);
+  const Ctrl prm = *ctrl;
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const CandEntry E = S.queue[e];
+    const double a = M.val[E.off];
+    const int32_t j = M.col[E.off];
+    double L, U;
+    float WU, WL;
+    uint32_t fl;
+    ld_rec(S.rec + j, L, U, WU, WL, fl);
+    RowView rv;
+    rv.minfin = E.minfin;
+    rv.maxfin = E.maxfin;
+    rv.lhs = E.lhs;
+    rv.rhs = E.rhs;
+    rv.mininf = E.mininf;
+    rv.maxinf = E.maxinf;
+    rv.thr_r = rv.thr_l = f_inf();
+    rv.exact = 0;
+    rv.act = 1;
+    nnz_candidates(a, j, L, U, fl, E.sides, rv, prm, S.keys, &S.ctrl->changed);
+  }
 }
 
 // ------------------------------------------------------------- k_round --
@@ -445,7 +464,6 @@ constexpr int kRoundWarps = 8;
 
 __global__ void __launch_bounds__(kRoundWarps * 32)
 k_round(DevMatrix M, DevState S) {
-  __shared__ WarpScratch scratch[kRoundWarps];
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
   const int wib = threadIdx.x >> 5;
@@ -549,8 +567,7 @@ k_round(DevMatrix M, DevState S) {
     rv.lhs = rv.rhs = 0.0;
   }
   const Ctrl prm = *ctrl;
-  warp_candidates(rv, t, mininf, maxinf, len, svp, scp, S.rec, prm, S.keys, &S.ctrl->changed,
-                  scratch[wib]);
+  warp_enqueue(rv, t, mininf, maxinf, len, sbase, M.val, M.col, S, prm);
 }
 
 // ------------------------------------------------------------ k_combine --
@@ -568,8 +585,8 @@ k_combine(DevMatrix M, DevState S) {
   double mnf = 0.0, mxf = 0.0;
   int32_t mni = 0, mxi = 0, ex = 0;
   float Tr = -f_inf(), Tl = -f_inf();
-  for (int32_t c = cb + lane; c < ce; c += kSliceW) {
-    Partial p = S.part[c];
+  for (int32_t q = cb + lane; q < ce; q += kSliceW) {
+    Partial p = S.part[M.split_cidx[q]];
     mnf += p.minfin;
     mxf += p.maxfin;
     mni += p.mininf;
@@ -618,7 +635,6 @@ k_combine(DevMatrix M, DevState S) {
 
 __global__ void __launch_bounds__(kRoundWarps * 32)
 k_cand_split(DevMatrix M, DevState S) {
-  __shared__ WarpScratch scratch[kRoundWarps];
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
   const int wib = threadIdx.x >> 5;
@@ -658,8 +674,7 @@ k_cand_split(DevMatrix M, DevState S) {
   }
   const int64_t sbase = M.slice_off[slice];
   const Ctrl prm = *ctrl;
-  warp_candidates(rv, t, cmin, cmax, len, M.val + sbase, M.col + sbase, S.rec, prm, S.keys,
-                  &S.ctrl->changed, scratch[wib]);
+  warp_enqueue(rv, t, cmin, cmax, len, sbase, M.val, M.col, S, prm);
 }
 
 // ------------------------------------------------------------- k_finish --
@@ -702,6 +717,7 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHand
       int32_t cont = (ch && !vc->infeasible && !vc->err && r < vc->max_rounds) ? 1 : 0;
       vc->last_changed = ch;
       vc->changed = 0;
+      vc->qcount = 0;
       vc->blocks_done = 0;
       __threadfence();
       if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
@@ -794,7 +810,7 @@ cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out, double
 
 // Launches one round's kernels on `st`.  In the graph body (use_cond = 1)
 // k_finish sets the WHILE condition; in the host-driven loop it does not.
-// With `ev` (8 events) each kernel is bracketed by a pair of events.
+// With `ev` (10 events) each kernel is bracketed by a pair of events.
 cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
                                  cudaGraphConditionalHandle handle, int use_cond, int num_sms,
                                  cudaStream_t st, cudaEvent_t *ev) {
@@ -817,6 +833,10 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const ui
     if (ev) cudaEventRecord(ev[5], st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (ev) cudaEventRecord(ev[8], st);
+  k_cand_queue<<<num_sms * 8, 256, 0, st>>>(M, S);
+  if (ev) cudaEventRecord(ev[9], st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int nbf = grid_for(M.n, kFinishThreads, num_sms * 8);
   if (ev) cudaEventRecord(ev[6], st);
   k_finish<<<nbf, kFinishThreads, 0, st>>>(S, vt_ws, M.n, handle, use_cond);

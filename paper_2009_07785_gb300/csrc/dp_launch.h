@@ -39,7 +39,7 @@ struct HostLayout {
   std::vector<int64_t> slice_off;
   std::vector<int32_t> slice_len;
   std::vector<int32_t> chunk_row, chunk_len, chunk_sidx;
-  std::vector<int32_t> split_row, split_cbeg;
+  std::vector<int32_t> split_row, split_cbeg, split_cidx;
 };
 
 // Validates a host CSR matrix and builds its layout.  Returns DP_OK,

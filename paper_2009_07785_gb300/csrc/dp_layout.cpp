@@ -63,7 +63,7 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
       for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
         if (!coef_screenable(val[k])) { rowflag[i] = kExactFlag; break; }
 
-    // split rows first, in row order, pieces in order
+    // pieces of the split rows, generated row by row (sorted below)
     std::vector<Chunk> chunks;
     chunks.reserve((size_t)m + (size_t)(nnz / chunk) + 1);
     int32_t nsplit = 0;
@@ -80,6 +80,24 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     }
     out.split_cbeg.push_back((int32_t)chunks.size());
     out.nsplit_rows = nsplit;
+    // sort the split chunks by length too (full chunks, then remainders,
+    // longest first) so that lanes of a slice do equal work; split_cidx maps
+    // each split row's pieces to their slots
+    {
+      const size_t ns = chunks.size();
+      std::vector<size_t> cnt2((size_t)chunk + 2, 0);
+      for (const Chunk &ch : chunks) cnt2[(size_t)(chunk - ch.len)]++;
+      std::vector<size_t> at2((size_t)chunk + 2, 0);
+      for (size_t b = 1; b < at2.size(); ++b) at2[b] = at2[b - 1] + cnt2[b - 1];
+      std::vector<Chunk> sorted(ns);
+      out.split_cidx.assign(ns, 0);
+      for (size_t q = 0; q < ns; ++q) {
+        size_t slot = at2[(size_t)(chunk - chunks[q].len)]++;
+        sorted[slot] = chunks[q];
+        out.split_cidx[q] = (int32_t)slot;
+      }
+      chunks.swap(sorted);
+    }
     // pad the split region to whole slices so no slice mixes both kinds
     while (chunks.size() % kSliceW) chunks.push_back({-1, 0, 0, 0, -1});
     const size_t nsplit_chunks = chunks.size();
