@@ -174,6 +174,49 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
                           double *ub_out, int32_t *infeasible, int32_t *rounds,
                           float *kernel_ms, int32_t *kernel_launches);
 
+/*
+ * Allocation-free propagation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory -- a solver
+ * whose device memory belongs to a pool allocator (a framework's caching
+ * allocator, the solver's own arena) that a stray cudaMalloc would fragment
+ * or exhaust, or a latency-critical pipeline in which cudaMalloc/cudaFree
+ * would synchronise the device.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * It propagates one problem given entirely in DEVICE memory of `device`:
+ * the CSR matrix (row_ptr[m+1] int64, col_idx[nnz] int32, val[nnz] binary64,
+ * same rules as dp_matrix_load), lb, ub, vartype, lhs, rhs, and the outputs
+ * lb_out, ub_out (which also hold the round state).  infeasible and rounds
+ * are HOST pointers; params as for dp_propagate (NULL = defaults).  Work is
+ * issued on `cuda_stream` (NULL = the legacy default stream); the host waits
+ * for the stream after every round (one thread per row, no screen), so this
+ * path is for callers that cannot allocate, not the fast path.
+ *
+ * Its only scratch -- the next-state bound keys and a control block -- is a
+ * file-scope device array sized for n <= DP_NOALLOC_MAX_VARS variables
+ * (16 MiB plus 256 bytes), which every GPU that loads the library holds
+ * until the process exits.  Larger n is rejected with DP_ERR_INVALID_ARG, as
+ * are host pointers where device pointers are required.  A malformed matrix
+ * returns DP_ERR_BAD_CSR and bad bounds or sides DP_ERR_NAN_INPUT; nothing
+ * is read out of range.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and each call
+ * re-initialises what it uses; calls whose GPU work can overlap (several
+ * streams or host threads) race on it and must be serialised by the caller.
+ * Results equal dp_propagate's.  Returns DP_OK, DP_CAP_HIT or an error.
+ */
+#define DP_NOALLOC_MAX_VARS (1 << 20)
+int dp_propagate_noalloc(int device, void *cuda_stream, int32_t m, int32_t n,
+                         int64_t nnz, const int64_t *row_ptr,
+                         const int32_t *col_idx, const double *val,
+                         const double *lb, const double *ub,
+                         const uint8_t *vartype, const double *lhs,
+                         const double *rhs, const dp_params *params,
+                         double *lb_out, double *ub_out, int32_t *infeasible,
+                         int32_t *rounds);
+
 #ifdef __cplusplus
 }
 #endif

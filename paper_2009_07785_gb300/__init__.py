@@ -30,7 +30,8 @@ DP_ERR_TIMEOUT = -6
 
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
-           "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop")
+           "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
+           "dp_propagate_noalloc")
 
 
 class dp_params(C.Structure):
@@ -73,6 +74,10 @@ def lib() -> C.CDLL:
                                         C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float),
                                         C.POINTER(i32)]
     L.dp_propagate_hostloop.restype = C.c_int
+    L.dp_propagate_noalloc.argtypes = [C.c_int, vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp,
+                                       C.POINTER(dp_params), vp, vp, C.POINTER(i32),
+                                       C.POINTER(i32)]
+    L.dp_propagate_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -252,3 +257,24 @@ def dp_propagate_hostloop(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
     return Result(lb_out, ub_out, inf.value, rounds.value, rc,
                   tuple(ms) if timing else None, tuple(cnt))
 
+
+NOALLOC_MAX_VARS = 1 << 20
+
+
+def dp_propagate_noalloc(device: int, stream, m: int, n: int, row_ptr, col_idx, val, lb, ub,
+                         vartype, lhs, rhs, lb_out, ub_out,
+                         params: dp_params | None = None) -> Result:
+    """Allocation-free propagation over a CSR matrix and problem already in
+    device memory (all array arguments are CUDA tensors; lb_out/ub_out are
+    caller-allocated).  For callers that must not allocate device memory;
+    its scratch is a fixed static device array (n <= NOALLOC_MAX_VARS)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    inf, rounds = C.c_int32(), C.c_int32()
+    nnz = int(col_idx.numel()) if hasattr(col_idx, "numel") else len(col_idx)
+    rc = _check(lib().dp_propagate_noalloc(
+        int(device), C.c_void_p(stream) if stream else None, int(m), int(n), nnz, _ptr(row_ptr),
+        _ptr(col_idx), _ptr(val), _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs), _ptr(rhs),
+        C.byref(params) if params is not None else None, _ptr(lb_out), _ptr(ub_out),
+        C.byref(inf), C.byref(rounds)), "dp_propagate_noalloc")
+    return Result(lb_out, ub_out, inf.value, rounds.value, rc)
