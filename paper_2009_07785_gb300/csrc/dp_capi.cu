@@ -265,16 +265,11 @@ int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
   TRY(dev_alloc(mat, &S.rhs, (size_t)m));
   TRY(dev_alloc(mat, &S.part, (size_t)H.nslices_split * dp::kSliceW));
   TRY(dev_alloc(mat, &S.rowtot, (size_t)H.nsplit_rows));
-  {
-    // candidate queue: a quarter of the slots (at least 1M entries) covers the
-    // survivors of the screen on the workloads measured; a full queue falls
-    // back to in-lane evaluation
-    int64_t cap = mat->padded / 4;
-    if (cap < (int64_t(1) << 20)) cap = int64_t(1) << 20;
-    if (cap > mat->padded) cap = mat->padded > 0 ? mat->padded : 1;
-    S.qcap = (int32_t)cap;
-    TRY(dev_alloc(mat, &S.queue, (size_t)cap));
-  }
+  // candidate queue: at most one entry per slot and round, so it never
+  // overflows; row sums are stored per chunk slot
+  TRY(dev_alloc(mat, &S.queue, (size_t)mat->padded));
+  TRY(dev_alloc(mat, &S.rowsum, (size_t)H.nslices * dp::kSliceW));
+  TRY(dev_alloc(mat, &S.side, (size_t)H.nslices * dp::kSliceW));
   TRY(dev_alloc(mat, &S.ctrl, 1));
   TRY(dev_alloc(mat, &mat->vt_ws, (size_t)n));
   TRY(dev_alloc(mat, &mat->st_lb, (size_t)n));
@@ -337,7 +332,7 @@ int begin_call(dp_ctx *ctx, dp_matrix *mat, const double *lb, const double *ub,
   hc->eps_feas = p.eps_feas;
   hc->inf_thr = p.inf_threshold;
   CUDA_TRY(cudaMemcpyAsync(mat->S.ctrl, hc, sizeof(*hc), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(dp::launch_prologue(mat->S, mat->vt_ws, m, n, d_lb, d_ub, d_vt, d_lhs, d_rhs,
+  CUDA_TRY(dp::launch_prologue(mat->M, mat->S, mat->vt_ws, m, n, d_lb, d_ub, d_vt, d_lhs, d_rhs,
                                p.eps_int, p.tau_rel, p.inf_threshold, ctx->num_sms, st));
   return DP_OK;
 }

@@ -12,6 +12,7 @@
 //   the row's CSR order.
 #pragma once
 #include <cstdint>
+#include <cuda_runtime.h>
 
 namespace dp {
 
@@ -32,9 +33,12 @@ static_assert(sizeof(VarRec) == 32, "VarRec must be one 32-byte sector");
 // Partial activity of one chunk of a split row.
 // Screen values of a chunk, per side: the largest (T1) and second largest
 // (T2) upper bounds on |a| W over the chunk, and the slot of the largest.
+// Also the slot of an infinite contribution to each activity (the one that
+// gets a finite residual when the row has exactly one, Sec. 3.4).
 struct Top2 {
   float r1, r2, l1, l2;
   int32_t kr, kl;
+  int32_t kinf_min, kinf_max;
 };
 
 struct alignas(16) Partial {
@@ -54,13 +58,20 @@ struct alignas(16) RowTot {
   int32_t row;
 };
 
-// One nonzero whose candidates survived the screen, with its row's sums,
-// queued for the lane-dense candidate kernel.
-struct alignas(16) CandEntry {
-  double minfin, maxfin, lhs, rhs;
+// One nonzero whose candidates survived the screen, queued for the
+// lane-dense candidate kernel: its element offset in val/col, and
+// (chunk slot << 2 | sides), sides bit 0 = right-hand side, bit 1 = left.
+// The queue holds one entry per slot at most, so it cannot overflow.
+struct alignas(8) CandEntry {
+  uint32_t off;
+  uint32_t cs;
+};
+
+// Activity sums of the row a queued chunk belongs to (written by the lane
+// that queues the chunk's first survivor; indexed by chunk slot).
+struct alignas(8) RowSum {
+  double minfin, maxfin;
   int32_t mininf, maxinf;
-  int32_t off;     // element offset of the nonzero in val/col
-  uint32_t sides;  // bit 0: right-hand side, bit 1: left-hand side
 };
 
 // Device control block of one propagation run.
@@ -96,12 +107,12 @@ struct DevMatrix {
 };
 
 struct DevState {
-  CandEntry *queue;     // [qcap] candidate queue
-  int32_t qcap;
-  int32_t pad;
+  CandEntry *queue;     // [padded slots] candidate queue
+  RowSum *rowsum;       // [chunk slots] sums of rows with queued nonzeros
   VarRec *rec;          // [n] state at the start of the round
   long long *keys;      // [2n] next state as order-preserving int64 keys
   double *lhs, *rhs;    // [m] normalised sides
+  double2 *side;        // [chunk slots] {lhs, rhs} of each chunk's row, in slot order
   Partial *part;        // [nslices_split*32]
   RowTot *rowtot;       // [nsplit_rows]
   Ctrl *ctrl;

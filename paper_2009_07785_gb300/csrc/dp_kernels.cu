@@ -316,6 +316,7 @@ __device__ __forceinline__ Top2 top2_init() {
   Top2 t;
   t.r1 = t.r2 = t.l1 = t.l2 = -f_inf();
   t.kr = t.kl = 0;
+  t.kinf_min = t.kinf_max = 0;
   return t;
 }
 
@@ -326,19 +327,18 @@ __device__ __forceinline__ Top2 top2_init() {
 // the second-largest screen value of a side is below the threshold, only the
 // chunk's largest can survive and it is queued directly (no re-read);
 // otherwise the lane re-reads its chunk (values and columns from L2, records
-// through the same gather), four slots at a time.  If the queue is full the
-// lane evaluates the nonzero itself (same result, divergent).  All 32 lanes
-// must call this (warp collectives).
+// through the same gather), four slots at a time.  All 32 lanes must call
+// this (warp collectives).
 __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t, int chunk_mininf,
-                                             int chunk_maxinf, int32_t mylen,
+                                             int chunk_maxinf, int32_t mylen, int64_t chunk_slot,
                                              int64_t slice_off_elems, const double *val,
-                                             const int32_t *col, const DevState &S,
-                                             const Ctrl &prm) {
+                                             const int32_t *col, const DevState &S) {
   const int lane = threadIdx.x & 31;
   const bool act = mine.act != 0;
   if (__ballot_sync(kFull, act) == 0u) return;
   const unsigned lt = (1u << lane) - 1u;
 
+  bool wrote_sums = false;
   auto push = [&](bool h, int k, unsigned sides) {
     const unsigned pm = __ballot_sync(kFull, h);
     if (pm == 0u) return;
@@ -347,50 +347,40 @@ __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t,
     if (lane == leader) base = atomicAdd(&S.ctrl->qcount, __popc(pm));
     base = __shfl_sync(kFull, base, leader);
     if (!h) return;
-    const int slot = base + __popc(pm & lt);
-    const int64_t off = slice_off_elems + (int64_t)k * kSliceW + lane;
-    if (slot < S.qcap) {
-      CandEntry e;
-      e.minfin = mine.minfin;
-      e.maxfin = mine.maxfin;
-      e.lhs = mine.lhs;
-      e.rhs = mine.rhs;
-      e.mininf = mine.mininf;
-      e.maxinf = mine.maxinf;
-      e.off = (int32_t)off;
-      e.sides = sides;
-      S.queue[slot] = e;
-    } else {
-      double a = val[off];
-      int32_t j = col[off];
-      double L, U;
-      float WU, WL;
-      uint32_t fl;
-      ld_rec(S.rec + j, L, U, WU, WL, fl);
-      nnz_candidates(a, j, L, U, fl, sides, mine, prm, S.keys, &S.ctrl->changed);
+    if (!wrote_sums) {
+      RowSum rs;
+      rs.minfin = mine.minfin;
+      rs.maxfin = mine.maxfin;
+      rs.mininf = mine.mininf;
+      rs.maxinf = mine.maxinf;
+      S.rowsum[chunk_slot] = rs;
+      wrote_sums = true;
     }
+    CandEntry e;
+    e.off = (uint32_t)(slice_off_elems + (int64_t)k * kSliceW + lane);
+    e.cs = ((uint32_t)chunk_slot << 2) | sides;
+    S.queue[base + __popc(pm & lt)] = e;
   };
 
-  const bool full = act && (mine.exact || (mine.mininf == 1 && chunk_mininf > 0) ||
-                            (mine.maxinf == 1 && chunk_maxinf > 0) || t.r2 > mine.thr_r ||
-                            t.l2 > mine.thr_l);
-  // only the largest screen value of a side can pass: queue it directly
+  // Survivors can be named without re-reading the chunk unless a side has
+  // two screen values above its threshold (or the row skips the screen).
+  // With exactly one infinite contribution to a side's activity, only that
+  // nonzero gets a finite residual on that side (Sec. 3.4); its slot was
+  // recorded by the activity pass.
+  const bool full = act && (mine.exact || (mine.mininf == 0 && t.r2 > mine.thr_r) ||
+                            (mine.maxinf == 0 && t.l2 > mine.thr_l));
   bool h1 = false, h2 = false;
   int k1 = 0, k2 = 0;
-  unsigned s1 = 0u;
   if (act && !full) {
-    const bool pr = t.r1 > mine.thr_r, pl = t.l1 > mine.thr_l;
-    if (pr && pl && t.kr == t.kl) {
-      h1 = true;
-      k1 = t.kr;
-      s1 = 3u;
-    } else {
-      if (pr) { h1 = true; k1 = t.kr; s1 = 1u; }
-      if (pl) { h2 = true; k2 = t.kl; }
-    }
+    const bool fr = d_isfinite(mine.rhs), fl = d_isfinite(mine.lhs);
+    if (fr && mine.mininf == 0 && t.r1 > mine.thr_r) { h1 = true; k1 = t.kr; }
+    if (fr && mine.mininf == 1 && chunk_mininf > 0) { h1 = true; k1 = t.kinf_min; }
+    if (fl && mine.maxinf == 0 && t.l1 > mine.thr_l) { h2 = true; k2 = t.kl; }
+    if (fl && mine.maxinf == 1 && chunk_maxinf > 0) { h2 = true; k2 = t.kinf_max; }
   }
-  push(h1, k1, s1);
-  push(h2, k2, 2u);
+  const bool merge = h1 && h2 && k1 == k2;
+  push(h1, k1, merge ? 3u : 1u);
+  push(h2 && !merge, k2, 2u);
 
   // full re-read of the chunk, four slots at a time
   const int len = full ? mylen : 0;
@@ -434,10 +424,13 @@ __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t,
 __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
-  const int32_t cnt = min(ctrl->qcount, S.qcap);
+  const int32_t cnt = ctrl->qcount;
   const Ctrl prm = *ctrl;
   for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
     const CandEntry E = S.queue[e];
+    const uint32_t c = E.cs >> 2;
+    const RowSum rs = S.rowsum[c];
+    const double2 sd = S.side[c];
     const double a = M.val[E.off];
     const int32_t j = M.col[E.off];
     double L, U;
@@ -445,24 +438,26 @@ __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
     uint32_t fl;
     ld_rec(S.rec + j, L, U, WU, WL, fl);
     RowView rv;
-    rv.minfin = E.minfin;
-    rv.maxfin = E.maxfin;
-    rv.lhs = E.lhs;
-    rv.rhs = E.rhs;
-    rv.mininf = E.mininf;
-    rv.maxinf = E.maxinf;
+    rv.minfin = rs.minfin;
+    rv.maxfin = rs.maxfin;
+    rv.mininf = rs.mininf;
+    rv.maxinf = rs.maxinf;
+    rv.lhs = sd.x;
+    rv.rhs = sd.y;
     rv.thr_r = rv.thr_l = f_inf();
     rv.exact = 0;
     rv.act = 1;
-    nnz_candidates(a, j, L, U, fl, E.sides, rv, prm, S.keys, &S.ctrl->changed);
+    nnz_candidates(a, j, L, U, fl, E.cs & 3u, rv, prm, S.keys, &S.ctrl->changed);
   }
 }
 
 // ------------------------------------------------------------- k_round --
 
 constexpr int kRoundWarps = 8;
+constexpr int kGroup = 4;         // slots per group in the activity loop
+constexpr int kRoundMinBlocks = 3;  // resident blocks per SM the register budget allows
 
-__global__ void __launch_bounds__(kRoundWarps * 32)
+__global__ void __launch_bounds__(kRoundWarps * 32, kRoundMinBlocks)
 k_round(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
@@ -484,53 +479,62 @@ k_round(DevMatrix M, DevState S) {
   double minfin = 0.0, maxfin = 0.0;
   int32_t mininf = 0, maxinf = 0;
   Top2 t = top2_init();
-  int k = 0;
-  for (; k + 4 <= len; k += 4) {
-    double a[4];
-    int32_t j[4];
+  // groups of kGroup slots: all loads and gathers of a group are issued
+  // before any is consumed, and the next group's values and columns are
+  // fetched while this group's gathers are in flight; the last group's
+  // missing slots are skipped (uniformly within a length-sorted slice)
+  double an[kGroup];
+  int32_t jn[kGroup];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      a[u] = __ldcs(vp + (int64_t)(k + u) * kSliceW);
-      j[u] = __ldcs(cp + (int64_t)(k + u) * kSliceW);
-    }
-    double L[4], U[4];
-    float WU[4], WL[4];
-    uint32_t fl[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) ld_rec(S.rec + j[u], L[u], U[u], WU[u], WL[u], fl[u]);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      bool pos = d_pos(a[u]);
-      double bmin = pos ? L[u] : U[u];
-      double bmax = pos ? U[u] : L[u];
-      bool imin = d_isinf(bmin), imax = d_isinf(bmax);
-      mininf += imin;
-      maxinf += imax;
-      minfin = fma(a[u], imin ? 0.0 : bmin, minfin);
-      maxfin = fma(a[u], imax ? 0.0 : bmax, maxfin);
-      float au = absup_fast(a[u]);
-      top2_add(__fmul_ru(au, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
-      top2_add(__fmul_ru(au, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
+  for (int u = 0; u < kGroup; ++u) {
+    an[u] = 1.0;
+    jn[u] = 0;
+    if (u < len) {
+      an[u] = __ldcs(vp + (int64_t)u * kSliceW);
+      jn[u] = __ldcs(cp + (int64_t)u * kSliceW);
     }
   }
-  for (; k < len; ++k) {
-    double a = __ldcs(vp + (int64_t)k * kSliceW);
-    int32_t j = __ldcs(cp + (int64_t)k * kSliceW);
-    double L, U;
-    float WU, WL;
-    uint32_t fl;
-    ld_rec(S.rec + j, L, U, WU, WL, fl);
-    bool pos = d_pos(a);
-    double bmin = pos ? L : U;
-    double bmax = pos ? U : L;
-    bool imin = d_isinf(bmin), imax = d_isinf(bmax);
-    mininf += imin;
-    maxinf += imax;
-    minfin = fma(a, imin ? 0.0 : bmin, minfin);
-    maxfin = fma(a, imax ? 0.0 : bmax, maxfin);
-    float au = absup_fast(a);
-    top2_add(__fmul_ru(au, pos ? WU : WL), k, t.r1, t.r2, t.kr);
-    top2_add(__fmul_ru(au, pos ? WL : WU), k, t.l1, t.l2, t.kl);
+  for (int k = 0; k < len; k += kGroup) {
+    double a[kGroup];
+    double L[kGroup], U[kGroup];
+    float WU[kGroup], WL[kGroup];
+    uint32_t fl[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      a[u] = an[u];
+      L[u] = U[u] = 0.0;
+      WU[u] = WL[u] = 0.0f;
+      if (k + u < len) ld_rec(S.rec + jn[u], L[u], U[u], WU[u], WL[u], fl[u]);
+    }
+    if (k + kGroup < len) {
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        an[u] = 1.0;
+        jn[u] = 0;
+        if (k + kGroup + u < len) {
+          an[u] = __ldcs(vp + (int64_t)(k + kGroup + u) * kSliceW);
+          jn[u] = __ldcs(cp + (int64_t)(k + kGroup + u) * kSliceW);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      if (k + u < len) {
+        bool pos = d_pos(a[u]);
+        double bmin = pos ? L[u] : U[u];
+        double bmax = pos ? U[u] : L[u];
+        bool imin = d_isinf(bmin), imax = d_isinf(bmax);
+        mininf += imin;
+        maxinf += imax;
+        if (imin) t.kinf_min = k + u;
+        if (imax) t.kinf_max = k + u;
+        minfin = fma(a[u], imin ? 0.0 : bmin, minfin);
+        maxfin = fma(a[u], imax ? 0.0 : bmax, maxfin);
+        float au = absup_fast(a[u]);
+        top2_add(__fmul_ru(au, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
+        top2_add(__fmul_ru(au, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
+      }
+    }
   }
   const bool exact = (lenf & kExactFlag) != 0;
   if (exact) t.r1 = t.r2 = t.l1 = t.l2 = f_inf();
@@ -560,14 +564,14 @@ k_round(DevMatrix M, DevState S) {
   rv.act = 0;
   rv.thr_r = rv.thr_l = f_inf();
   if (row >= 0) {
-    rv.lhs = S.lhs[row];
-    rv.rhs = S.rhs[row];
+    const double2 sd = S.side[c];  // coalesced: sides stored in slot order
+    rv.lhs = sd.x;
+    rv.rhs = sd.y;
     row_sides(rv, t.r1, t.l1, ctrl->eps_feas, &S.ctrl->infeasible);
   } else {
     rv.lhs = rv.rhs = 0.0;
   }
-  const Ctrl prm = *ctrl;
-  warp_enqueue(rv, t, mininf, maxinf, len, sbase, M.val, M.col, S, prm);
+  warp_enqueue(rv, t, mininf, maxinf, len, c, sbase, M.val, M.col, S);
 }
 
 // ------------------------------------------------------------ k_combine --
@@ -673,8 +677,7 @@ k_cand_split(DevMatrix M, DevState S) {
     }
   }
   const int64_t sbase = M.slice_off[slice];
-  const Ctrl prm = *ctrl;
-  warp_enqueue(rv, t, cmin, cmax, len, sbase, M.val, M.col, S, prm);
+  warp_enqueue(rv, t, cmin, cmax, len, c, sbase, M.val, M.col, S);
 }
 
 // ------------------------------------------------------------- k_finish --
@@ -774,6 +777,26 @@ __global__ void k_prologue(DevState S, uint8_t *vt_ws, int32_t m, int32_t n,
   }
 }
 
+// Copies the normalised sides of each chunk's row into slot order, so that
+// the round kernel reads them coalesced.
+__global__ void k_prologue_sides(DevMatrix M, DevState S, const double *lhs, const double *rhs,
+                                 double thr) {
+  const double pinf = __longlong_as_double(0x7FF0000000000000ll);
+  const int64_t nslots = (int64_t)M.nslices * kSliceW;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nslots;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t row = M.chunk_row[c];
+    double l = 0.0, r = 0.0;
+    if (row >= 0) {
+      l = lhs[row];
+      r = rhs[row];
+      if (l <= -thr) l = -pinf;
+      if (r >= thr) r = pinf;
+    }
+    S.side[c] = make_double2(l, r);
+  }
+}
+
 __global__ void k_epilogue(DevState S, int32_t n, double *lb_out, double *ub_out) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -792,14 +815,22 @@ static int grid_for(int64_t work, int threads, int max_blocks) {
   return (int)b;
 }
 
-cudaError_t launch_prologue(const DevState &S, uint8_t *vt_ws, int32_t m, int32_t n,
-                            const double *lb, const double *ub, const uint8_t *vartype,
-                            const double *lhs, const double *rhs, double eps_int,
-                            double tau_rel, double thr, int num_sms, cudaStream_t st) {
+cudaError_t launch_prologue(const DevMatrix &M, const DevState &S, uint8_t *vt_ws, int32_t m,
+                            int32_t n, const double *lb, const double *ub,
+                            const uint8_t *vartype, const double *lhs, const double *rhs,
+                            double eps_int, double tau_rel, double thr, int num_sms,
+                            cudaStream_t st) {
   int64_t total = n > m ? n : m;
   k_prologue<<<grid_for(total, 256, num_sms * 16), 256, 0, st>>>(
       S, vt_ws, m, n, lb, ub, vartype, lhs, rhs, eps_int, tau_rel, thr);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (m > 0) {
+    k_prologue_sides<<<grid_for((int64_t)M.nslices * kSliceW, 256, num_sms * 16), 256, 0, st>>>(
+        M, S, lhs, rhs, thr);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out, double *ub_out,

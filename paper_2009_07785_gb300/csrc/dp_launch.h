@@ -9,8 +9,8 @@
 
 namespace dp {
 
-cudaError_t launch_prologue(const DevState &S, uint8_t *vt_ws, int32_t m,
-                            int32_t n, const double *lb, const double *ub,
+cudaError_t launch_prologue(const DevMatrix &M, const DevState &S, uint8_t *vt_ws,
+                            int32_t m, int32_t n, const double *lb, const double *ub,
                             const uint8_t *vartype, const double *lhs,
                             const double *rhs, double eps_int, double tau_rel,
                             double thr, int num_sms, cudaStream_t st);

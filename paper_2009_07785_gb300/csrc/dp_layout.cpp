@@ -121,6 +121,9 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     while (chunks.size() % kSliceW) chunks.push_back({-1, 0, 0, 0, -1});
 
     const size_t nslots = chunks.size();
+    // queue entries pack the chunk slot in 30 bits and the element offset
+    // in 32 bits
+    if (nslots >= (size_t(1) << 30)) return DP_ERR_INVALID_ARG;
     out.nslices = (int32_t)(nslots / kSliceW);
     out.nslices_split = (int32_t)(nsplit_chunks / kSliceW);
     out.slice_off.resize(out.nslices);
