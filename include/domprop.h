@@ -217,6 +217,60 @@ int dp_propagate_noalloc(int device, void *cuda_stream, int32_t m, int32_t n,
                          double *lb_out, double *ub_out, int32_t *infeasible,
                          int32_t *rounds);
 
+/*
+ * Propagates `count` branch-and-bound nodes over one loaded matrix: each
+ * node is its own bound vector, and each is propagated exactly as
+ * dp_propagate would propagate it alone (same rounds, same results), with
+ * all nodes of a launch sharing the device-side round loop.  The paper
+ * (Sec. 5) points at propagation after branching -- many nodes, each a few
+ * bound changes away from a propagated state -- as the solver use that
+ * needs new parent methods on a GPU; its constraint marking (Alg. 1,
+ * Sec. 2.1) is applied per node: after round 1 a row is processed for a
+ * node only when one of its variables changed for that node.
+ * Inputs (host or device; not modified):
+ *   lb[count*n], ub[count*n]  binary64 bounds, node-major: node k's vector
+ *                             is lb[k*n .. k*n+n-1]
+ *   vartype[n], lhs[m], rhs[m], params   shared by all nodes, as in
+ *                             dp_propagate
+ * Outputs (host or device, caller-allocated, node-major like the inputs):
+ *   lb_out[count*n], ub_out[count*n]  bounds after each node's last round
+ *   infeasible[count], rounds[count]  HOST int32, per node, as in dp_propagate
+ *   status[count]     HOST int32 or NULL: 1 if the node stopped at the round
+ *                     cap with its last round still changing a bound
+ * Nodes run in launches of up to 1024 (fewer when n is large: entry
+ * indices node + j*nodes stay below 2^30); 32 nodes share each warp, so
+ * counts that are multiples of 32 use the device best.  The first call
+ * allocates a workspace of about 80 bytes per (variable, node) pair kept
+ * with the matrix (freed by dp_matrix_free); host inputs are staged.
+ * Returns DP_OK, DP_CAP_HIT (some node hit the cap), DP_ERR_INVALID_ARG,
+ * DP_ERR_NAN_INPUT (any node), DP_ERR_OOM or DP_ERR_CUDA.
+ */
+int dp_propagate_nodes(dp_ctx *ctx, const dp_matrix *mat, int32_t count,
+                       const double *lb, const double *ub,
+                       const uint8_t *vartype, const double *lhs,
+                       const double *rhs, const dp_params *params,
+                       double *lb_out, double *ub_out, int32_t *infeasible,
+                       int32_t *rounds, int32_t *status);
+
+/*
+ * dp_propagate_nodes with the round loop driven from the host (one stream
+ * synchronisation per round) so that each stage of a round can be timed;
+ * same results.  kernel_ms[6] (HOST, may be NULL) receives the summed
+ * CUDA-event time of each stage over all rounds and launches, in the order
+ * mark, mark_split, act, combine, cand_split, finish; kernel_launches[6]
+ * (HOST, may be NULL) how often each ran (stages 1, 3, 4 run only for
+ * matrices with split rows).  A measuring aid: the paper has no
+ * counterpart.
+ */
+int dp_propagate_nodes_hostloop(dp_ctx *ctx, const dp_matrix *mat,
+                                int32_t count, const double *lb,
+                                const double *ub, const uint8_t *vartype,
+                                const double *lhs, const double *rhs,
+                                const dp_params *params, double *lb_out,
+                                double *ub_out, int32_t *infeasible,
+                                int32_t *rounds, int32_t *status,
+                                float *kernel_ms, int32_t *kernel_launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,8 @@ DP_ERR_TIMEOUT = -6
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
            "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
-           "dp_propagate_noalloc")
+           "dp_propagate_noalloc", "dp_propagate_nodes",
+           "dp_propagate_nodes_hostloop")
 
 
 class dp_params(C.Structure):
@@ -78,6 +79,13 @@ def lib() -> C.CDLL:
                                        C.POINTER(dp_params), vp, vp, C.POINTER(i32),
                                        C.POINTER(i32)]
     L.dp_propagate_noalloc.restype = C.c_int
+    L.dp_propagate_nodes.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp,
+                                     vp, vp, vp]
+    L.dp_propagate_nodes.restype = C.c_int
+    L.dp_propagate_nodes_hostloop.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp,
+                                              C.POINTER(dp_params), vp, vp, vp, vp, vp,
+                                              C.POINTER(C.c_float), C.POINTER(i32)]
+    L.dp_propagate_nodes_hostloop.restype = C.c_int
     _lib = L
     return L
 
@@ -278,3 +286,60 @@ def dp_propagate_noalloc(device: int, stream, m: int, n: int, row_ptr, col_idx, 
         C.byref(params) if params is not None else None, _ptr(lb_out), _ptr(ub_out),
         C.byref(inf), C.byref(rounds)), "dp_propagate_noalloc")
     return Result(lb_out, ub_out, inf.value, rounds.value, rc)
+
+
+@dataclass
+class NodesResult:
+    lb: object            # [count, n] bounds after each node's last round
+    ub: object
+    infeasible: np.ndarray  # int32 [count]
+    rounds: np.ndarray      # int32 [count]
+    cap_hit: np.ndarray     # int32 [count]: stopped by the round cap
+    status: int             # DP_OK or DP_CAP_HIT (some node hit the cap)
+    kernel_ms: tuple | None = None        # host loop only: per-stage totals
+    kernel_launches: tuple | None = None  # host loop only: per-stage counts
+
+
+NODE_STAGES = ("mark", "mark_split", "act", "combine", "cand_split", "finish")
+
+
+def dp_propagate_nodes(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
+                       params: dp_params | None = None, lb_out=None, ub_out=None) -> NodesResult:
+    """Propagates a batch of branch-and-bound nodes over one matrix.  lb, ub
+    are [count, n] (node-major; numpy or torch, host or CUDA); each node's
+    result equals dp_propagate on that node alone."""
+    return _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, None)
+
+
+def dp_propagate_nodes_hostloop(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
+                                params: dp_params | None = None, lb_out=None,
+                                ub_out=None) -> NodesResult:
+    """dp_propagate_nodes with a host-driven round loop and per-stage
+    CUDA-event timings (NodesResult.kernel_ms / kernel_launches, in the order
+    of NODE_STAGES)."""
+    return _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, True)
+
+
+def _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, hostloop):
+    count = int(lb.shape[0]) if len(lb.shape) == 2 else 0
+    if len(lb.shape) != 2 or tuple(ub.shape) != tuple(lb.shape) or int(lb.shape[1]) != mat.n:
+        raise ValueError("lb and ub must both have shape [count, n]")
+    if lb_out is None:
+        lb_out = _like(lb, (count, mat.n))
+    if ub_out is None:
+        ub_out = _like(lb, (count, mat.n))
+    inf = np.zeros(max(count, 1), dtype=np.int32)
+    rounds = np.zeros(max(count, 1), dtype=np.int32)
+    cap = np.zeros(max(count, 1), dtype=np.int32)
+    args = (ctx.handle, mat.handle, count, _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs),
+            _ptr(rhs), C.byref(params) if params is not None else None, _ptr(lb_out),
+            _ptr(ub_out), inf.ctypes.data, rounds.ctypes.data, cap.ctypes.data)
+    if hostloop:
+        ms = (C.c_float * len(NODE_STAGES))()
+        cnt = (C.c_int32 * len(NODE_STAGES))()
+        rc = _check(lib().dp_propagate_nodes_hostloop(*args, ms, cnt),
+                    "dp_propagate_nodes_hostloop")
+        return NodesResult(lb_out, ub_out, inf[:count], rounds[:count], cap[:count], rc,
+                           tuple(ms), tuple(cnt))
+    rc = _check(lib().dp_propagate_nodes(*args), "dp_propagate_nodes")
+    return NodesResult(lb_out, ub_out, inf[:count], rounds[:count], cap[:count], rc)

@@ -23,7 +23,7 @@ LIB = LIBDIR / "libdomprop.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
               "--cudart", "shared", "-I", str(ROOT / "include")]
-SOURCES = ["dp_kernels.cu", "dp_capi.cu", "dp_layout.cpp", "dp_noalloc.cu"]
+SOURCES = ["dp_kernels.cu", "dp_capi.cu", "dp_layout.cpp", "dp_noalloc.cu", "dp_batch.cu"]
 
 
 def nvcc() -> str:
@@ -35,7 +35,8 @@ def nvcc() -> str:
 
 def _inputs() -> list[Path]:
     files = [CSRC / s for s in SOURCES]
-    files += sorted(CSRC.glob("*.h")) + sorted((ROOT / "include").glob("*.h"))
+    files += sorted(CSRC.glob("*.h")) + sorted(CSRC.glob("*.cuh"))
+    files += sorted((ROOT / "include").glob("*.h"))
     return files
 
 

@@ -1,0 +1,981 @@
+// Batched propagation of branch-and-bound nodes: many bound vectors over
+// one matrix in one graph-driven round loop.  The paper propagates one
+// problem per call and notes (Sec. 5) that after branching a solver
+// propagates from an already propagated state with a few bound changes;
+// a throughput device is fed by running many such nodes at once.
+//
+// Every node follows exactly the round-synchronous algorithm of the single
+// instance path (Alg. 2 with Jacobi rounds): the same activities (Def. 1,
+// Eq. 2a/2b, with the infinity counts of Sec. 3.4), the same candidates
+// (Eq. 3a/3b in the residual form of Eq. 5a/5b), the same integer rounding
+// and acceptance threshold, and its own termination and round count.
+//
+// Layout.  Bounds are node-minor (entry e = j*Bp + node).  The 32 lanes of
+// a warp are the 32 nodes of one node group; a warp walks one chunk of the
+// sliced-ELL matrix with warp-uniform loads of its values and columns and
+// one coalesced 512-byte load of the 32 nodes' bounds per nonzero.  The
+// side pattern of a row is warp-uniform, so a row with one infinite side
+// computes only the activity its finite side needs.
+//
+// Marking (the constraint marking of Alg. 1, Sec. 2.1).  In round r > 1 a
+// row is processed for a node only if a bound of one of its variables
+// changed for that node in round r-1.  Skipping the other rows is exact:
+// their activities, hence their candidates, are those of round r-1, which
+// were then applied or rejected against bounds that have not moved since.
+//
+// Round kernels (graph body):
+//   k_bmark        thread per chunk: the nodes that must process it (OR of
+//                  the change masks of its variables); work lists per group
+//   k_bmark_split  warp per split row: all chunks of a split row get the
+//                  row's mask
+//   k_bact         warp per work item: activities; for whole rows also
+//                  Step 2, the binary32 screen and the candidates with
+//                  filtered 64-bit atomics
+//   k_bcombine     warp per (split row, group): sums chunk partials in
+//                  chunk order, Step 2 and screen thresholds
+//   k_bcand_split  warp per (split chunk, group): candidates of split rows
+//   k_bfinish      thread per improved entry: commit, crossing test, change
+//                  masks; the last block ends nodes and sets the condition
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cfloat>
+
+#include "dp_device.cuh"
+#include "dp_internal.h"
+#include "dp_launch.h"
+#include "../../include/domprop.h"
+
+namespace dp {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kActWarps = 8;
+
+struct BParams {
+  int32_t Bp, G, Gs, round, max_rounds, err;
+  double eps_int, tau_rel, eps_feas, inf_thr;
+  float tau_dn, eps_dn;
+};
+
+__device__ __forceinline__ BParams load_params(const BCtrl *c) {
+  BParams P;
+  P.Bp = c->Bp;
+  P.G = c->G;
+  P.Gs = (c->G + 3) & ~3;
+  P.round = c->round;
+  P.max_rounds = c->max_rounds;
+  P.err = c->err;
+  P.eps_int = c->eps_int;
+  P.tau_rel = c->tau_rel;
+  P.eps_feas = c->eps_feas;
+  P.inf_thr = c->inf_thr;
+  P.tau_dn = f32_dn(c->tau_rel);
+  P.eps_dn = f32_dn(c->eps_int);
+  return P;
+}
+
+// Bounds {L, U} of one (variable, node) entry; read-only within a kernel.
+__device__ __forceinline__ double2 ld_bounds(const double2 *p) {
+  double2 v;
+  asm("ld.global.nc.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint4 or4(uint4 a, uint4 b) {
+  return make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w);
+}
+__device__ __forceinline__ uint32_t word4(const uint4 &v, int u) {
+  return u == 0 ? v.x : (u == 1 ? v.y : (u == 2 ? v.z : v.w));
+}
+
+// Appends `e` for every lane with h set (warp-aggregated); all 32 lanes call.
+template <typename T>
+__device__ __forceinline__ void warp_append(bool h, T e, T *list, int32_t *count) {
+  const unsigned m = __ballot_sync(kFull, h);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  if (h) list[base + __popc(m & ((1u << lane) - 1u))] = e;
+}
+
+// Sets, in bits[g], the bits of the lanes (nodes g*32 + lane) with h set.
+// The word only gains bits, so reading it first (possibly stale) saves the
+// atomic in the common case that the bits are already there.  All 32 lanes
+// call.
+__device__ __forceinline__ void note_nodes(uint32_t *bits, int g, bool h) {
+  const unsigned m = __ballot_sync(kFull, h);
+  if (m == 0u) return;
+  if ((threadIdx.x & 31) == 0 && (bits[g] & m) != m) atomicOr(&bits[g], m);
+}
+
+// Entries improved in a round are staged per warp in shared memory and
+// appended to the global dirty list in bulk, one counter atomic per
+// kStage entries rather than one per warp instruction.
+constexpr int kStage = 128;
+
+struct DirtyStage {
+  uint32_t *buf;  // this warp's shared-memory buffer
+  int n;          // staged entries (warp-uniform)
+};
+
+__device__ __forceinline__ void stage_flush(DirtyStage &st, uint32_t *list, int32_t *count) {
+  __syncwarp();
+  if (st.n == 0) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(count, st.n);
+  base = __shfl_sync(kFull, base, 0);
+  for (int i = lane; i < st.n; i += 32) list[base + i] = st.buf[i];
+  __syncwarp();
+  st.n = 0;
+}
+
+__device__ __forceinline__ void stage_push(DirtyStage &st, bool h, uint32_t e, uint32_t *list,
+                                           int32_t *count) {
+  const unsigned m = __ballot_sync(kFull, h);
+  if (m == 0u) return;
+  if (st.n + 32 > kStage) stage_flush(st, list, count);
+  const int lane = threadIdx.x & 31;
+  if (h) st.buf[st.n + __popc(m & ((1u << lane) - 1u))] = e;
+  st.n += __popc(m);
+}
+
+// Activity of one chunk for this lane's node (Def. 1 / Eq. 2a, 2b; an
+// infinite contribution is counted, not summed, Sec. 3.4), plus the
+// largest binary32 screen value of each needed side.  The sums are one
+// FMA chain per side in the chunk's CSR order.
+struct BAct {
+  double minfin, maxfin;
+  int32_t mininf, maxinf;
+  float tr, tl;
+};
+
+__device__ __forceinline__ void act_add(double a, double2 b, uint8_t t, bool need_min,
+                                        bool need_max, bool screen, const BParams &P,
+                                        BAct &r) {
+  const bool pos = d_pos(a);
+  const double bmin = pos ? b.x : b.y;
+  const double bmax = pos ? b.y : b.x;
+  if (need_min) {
+    const bool i = d_isinf(bmin);
+    r.mininf += i ? 1 : 0;
+    r.minfin = fma(a, i ? 0.0 : bmin, r.minfin);
+  }
+  if (need_max) {
+    const bool i = d_isinf(bmax);
+    r.maxinf += i ? 1 : 0;
+    r.maxfin = fma(a, i ? 0.0 : bmax, r.maxfin);
+  }
+  if (screen) {
+    float WU, WL;
+    screen_widths(b.x, b.y, t != 0, P.tau_dn, P.eps_dn, WU, WL);
+    const float au = absup_fast(a);
+    if (need_min) r.tr = fmaxf(r.tr, __fmul_ru(au, pos ? WU : WL));
+    if (need_max) r.tl = fmaxf(r.tl, __fmul_ru(au, pos ? WL : WU));
+  }
+}
+
+__device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchState &S,
+                                               int64_t base, int len, int node, bool need_min,
+                                               bool need_max, bool screen, const BParams &P) {
+  BAct r;
+  r.minfin = r.maxfin = 0.0;
+  r.mininf = r.maxinf = 0;
+  r.tr = r.tl = -f_inf();
+  const double *vp = M.val + base;
+  const int32_t *cp = M.col + base;
+  const double2 *bp = S.cur + node;
+  int k = 0;
+  for (; k + 4 <= len; k += 4) {
+    double a[4];
+    int32_t j[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = __ldg(vp + (int64_t)(k + u) * kSliceW);
+      j[u] = __ldg(cp + (int64_t)(k + u) * kSliceW);
+    }
+    double2 b[4];
+    uint8_t t[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      b[u] = ld_bounds(bp + (int64_t)j[u] * P.Bp);
+      t[u] = screen ? __ldg(S.vt + j[u]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) act_add(a[u], b[u], t[u], need_min, need_max, screen, P, r);
+  }
+  for (; k < len; ++k) {
+    const double a = __ldg(vp + (int64_t)k * kSliceW);
+    const int32_t j = __ldg(cp + (int64_t)k * kSliceW);
+    const double2 b = ld_bounds(bp + (int64_t)j * P.Bp);
+    const uint8_t t = screen ? __ldg(S.vt + j) : 0;
+    act_add(a, b, t, need_min, need_max, screen, P, r);
+  }
+  if (!screen) r.tr = r.tl = f_inf();
+  return r;
+}
+
+// Candidates of one nonzero for one node (Eq. 3a/3b via Eq. 5a/5b, Step 3
+// rounding, the acceptance threshold), applied with order-preserving 64-bit
+// atomics to the node's next state kp = {lower key, upper key}.  Returns
+// whether this lane made the first improvement of the entry in this round
+// (the atomic saw the start-of-round key), which puts the entry on the
+// dirty list exactly once per side.
+__device__ __forceinline__ bool bnnz_candidates(double a, bool isint, double L, double U,
+                                                unsigned sides, const RowView &rv,
+                                                const BParams &P, long long *kp) {
+  const bool pos = d_pos(a);
+  const double bmin = pos ? L : U;
+  const double bmax = pos ? U : L;
+  double lc = 0.0, uc = 0.0;
+  bool hl = false, hu = false;
+  if (sides & 1u) {
+    const double res = (rv.mininf == 0) ? fma(-a, bmin, rv.minfin) : rv.minfin;
+    if (d_isfinite(res)) {
+      const double c = (rv.rhs - res) / a;
+      if (pos) { uc = c; hu = true; } else { lc = c; hl = true; }
+    }
+  }
+  if (sides & 2u) {
+    const double res = (rv.maxinf == 0) ? fma(-a, bmax, rv.maxfin) : rv.maxfin;
+    if (d_isfinite(res)) {
+      const double c = (rv.lhs - res) / a;
+      if (pos) { lc = c; hl = true; } else { uc = c; hu = true; }
+    }
+  }
+  // rounding, the infinity threshold and the acceptance tests follow the
+  // binary64 formulas exactly; comparisons, floor/ceil and max(1, |x|) run
+  // on the integer pipe (see the helpers), the sums and products in binary64
+  if (hl) {
+    if (isint) lc = d_ceil_int(lc - P.eps_int);
+    if (!d_abs_lt(lc, P.inf_thr)) hl = false;
+  }
+  if (hu) {
+    if (isint) uc = d_floor_int(uc + P.eps_int);
+    if (!d_abs_lt(uc, P.inf_thr)) hu = false;
+  }
+  bool first = false;
+  if (hl) {
+    bool acc;
+    if (d_is_neginf(L)) acc = true;
+    else if (isint) acc = cmp_key(lc) > cmp_key(L);
+    else acc = cmp_key(lc) > cmp_key(L + P.tau_rel * d_max1abs(L));
+    if (acc) {
+      const long long nk = key_of(lc), k0 = key_of(L);
+      const long long old = atomicMax(&kp[0], nk);
+      first |= (old == k0 && nk > old);
+    }
+  }
+  if (hu) {
+    bool acc;
+    if (d_is_posinf(U)) acc = true;
+    else if (isint) acc = cmp_key(uc) < cmp_key(U);
+    else acc = cmp_key(uc) < cmp_key(U - P.tau_rel * d_max1abs(U));
+    if (acc) {
+      const long long nk = key_of(uc), k0 = key_of(U);
+      const long long old = atomicMin(&kp[1], nk);
+      first |= (old == k0 && nk < old);
+    }
+  }
+  return first;
+}
+
+// Nonzero-node pairs that survived the screen wait in a per-warp buffer and
+// are evaluated 32 at a time, one pair per lane, so that the binary64
+// candidate formulas (two divisions) run lane-dense whatever the pattern of
+// survivors across the 32 nodes of a warp.  Each entry carries its own
+// context, so a batch may mix pairs of several rows.
+constexpr int kPairCap = 64;
+
+struct PairBuf {
+  uint32_t off[kPairCap];   // element offset of the nonzero in val/col
+  uint32_t info[kPairCap];  // node << 4 | maxinf==0 << 3 | mininf==0 << 2 | sides
+  int32_t row[kPairCap];
+  double minfin[kPairCap], maxfin[kPairCap];
+};
+
+struct PairQueue {
+  PairBuf *buf;  // this warp's shared-memory buffer
+  int n;         // buffered pairs (warp-uniform)
+};
+
+// Evaluates pairs [from, from + count) of the buffer, count <= 32.  All 32
+// lanes call.
+__device__ __forceinline__ void eval_pairs(PairQueue &pq, int from, int count,
+                                           const DevMatrix &M, const BatchState &S,
+                                           const BParams &P, DirtyStage &st, uint32_t *dirty,
+                                           int32_t *ndirty) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  bool first = false;
+  uint32_t e = 0u;
+  if (lane < count) {
+    const int q = from + lane;
+    const PairBuf &B = *pq.buf;
+    const uint32_t off = B.off[q], info = B.info[q];
+    const int32_t row = B.row[q];
+    const uint32_t node = info >> 4;
+    RowView rv;
+    rv.minfin = B.minfin[q];
+    rv.maxfin = B.maxfin[q];
+    rv.mininf = (info & 4u) ? 0 : 1;
+    rv.maxinf = (info & 8u) ? 0 : 1;
+    rv.lhs = S.lhs[row];
+    rv.rhs = S.rhs[row];
+    const double a = __ldg(M.val + off);
+    const int32_t j = __ldg(M.col + off);
+    e = (uint32_t)((int64_t)j * P.Bp + node);
+    const double2 b = ld_bounds(S.cur + e);
+    const bool isint = __ldg(S.vt + j) != 0;
+    first = bnnz_candidates(a, isint, b.x, b.y, info & 3u, rv, P, S.nkey + 2 * (int64_t)e);
+  }
+  __syncwarp();
+  stage_push(st, first, e, dirty, ndirty);
+}
+
+// Candidates of one chunk for this lane's node; `on` = the node processes
+// the chunk and its row may yield an accepted candidate.  The screen is
+// recomputed from the bounds (binary32 and integer work, which overlaps
+// with the loads), so binary64 candidate work runs only for nonzeros that
+// can tighten.  All 32 lanes call.
+__device__ __forceinline__ void chunk_candidates(const DevMatrix &M, const BatchState &S,
+                                                 int64_t base, int len, int node, bool on,
+                                                 int32_t row, const RowView &rv,
+                                                 const BParams &P, PairQueue &pq,
+                                                 DirtyStage &st, uint32_t *dirty,
+                                                 int32_t *ndirty) {
+  const int lane = threadIdx.x & 31;
+  const double *vp = M.val + base;
+  const int32_t *cp = M.col + base;
+  const uint32_t ctx = ((uint32_t)node << 4) | (rv.maxinf == 0 ? 8u : 0u) |
+                       (rv.mininf == 0 ? 4u : 0u);
+  for (int k = 0; k < len; ++k) {
+    const double a = __ldg(vp + (int64_t)k * kSliceW);
+    const int32_t j = __ldg(cp + (int64_t)k * kSliceW);
+    unsigned sides = 0u;
+    if (on) {
+      const double2 b = ld_bounds(S.cur + (int64_t)j * P.Bp + node);
+      float WU = f_inf(), WL = f_inf();
+      if (!rv.exact) screen_widths(b.x, b.y, __ldg(S.vt + j) != 0, P.tau_dn, P.eps_dn, WU, WL);
+      sides = nnz_sides(a, b.x, b.y, WU, WL, rv);
+    }
+    const unsigned m = __ballot_sync(kFull, sides != 0u);
+    if (m == 0u) continue;
+    if (sides) {
+      const int q = pq.n + __popc(m & ((1u << lane) - 1u));
+      PairBuf &B = *pq.buf;
+      B.off[q] = (uint32_t)(base + (int64_t)k * kSliceW);
+      B.info[q] = ctx | sides;
+      B.row[q] = row;
+      B.minfin[q] = rv.minfin;
+      B.maxfin[q] = rv.maxfin;
+    }
+    pq.n += __popc(m);
+    if (pq.n >= 32) {
+      pq.n -= 32;
+      eval_pairs(pq, pq.n, 32, M, S, P, st, dirty, ndirty);
+    }
+  }
+}
+
+// Evaluates what is left in the pair buffer (end of a warp's work).
+__device__ __forceinline__ void drain_pairs(PairQueue &pq, const DevMatrix &M,
+                                            const BatchState &S, const BParams &P,
+                                            DirtyStage &st, uint32_t *dirty, int32_t *ndirty) {
+  if (pq.n > 0) eval_pairs(pq, 0, pq.n, M, S, P, st, dirty, ndirty);
+  pq.n = 0;
+  stage_flush(st, dirty, ndirty);
+}
+
+// ------------------------------------------------------------- k_bmark --
+
+__global__ void __launch_bounds__(kThreads) k_bmark(DevMatrix M, BatchState S) {
+  BCtrl *ctrl = S.ctrl;
+  const BParams P = load_params(ctrl);
+  if (P.err) return;
+  const int p = P.round & 1;
+  const bool first = P.round == 0;
+  const uint32_t *chg = S.chg[p];
+  const int64_t nslots = S.nslots;
+  const int64_t split_slots = (int64_t)M.nslices_split * kSliceW;
+  for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < nslots;
+       c0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cs = c0 + threadIdx.x;
+    int32_t row = -1, len = 0;
+    int64_t base = 0;
+    bool used = false;  // a free row (both sides infinite) has no candidates
+                        // and cannot be infeasible: it is never processed
+    if (cs < nslots) {
+      row = M.chunk_row[cs];
+      if (row >= 0) {
+        len = M.chunk_len[cs] & kLenMask;
+        base = M.slice_off[cs / kSliceW] + (cs % kSliceW);
+        used = d_isfinite(S.lhs[row]) || d_isfinite(S.rhs[row]);
+      }
+    }
+    const bool split = cs < split_slots;
+    for (int gq = 0; gq < P.Gs; gq += 4) {
+      uint4 m = make_uint4(0u, 0u, 0u, 0u);
+      if (row >= 0) {
+        if (!used) {
+        } else if (first) {
+          m = make_uint4(kFull, kFull, kFull, kFull);
+        } else {
+          for (int k = 0; k < len; ++k) {
+            const int32_t j = M.col[base + (int64_t)k * kSliceW];
+            m = or4(m, *reinterpret_cast<const uint4 *>(chg + (int64_t)j * P.Gs + gq));
+          }
+        }
+        const uint4 al = *reinterpret_cast<const uint4 *>(S.alive + gq);
+        m = make_uint4(m.x & al.x, m.y & al.y, m.z & al.z, m.w & al.w);
+        *reinterpret_cast<uint4 *>(S.cmask + cs * P.Gs + gq) = m;
+      }
+      if (!split) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int g = gq + u;
+          if (g < P.G)  // uniform
+            warp_append<int32_t>(used && word4(m, u) != 0u, (int32_t)cs,
+                                 S.items + (int64_t)g * nslots, &ctrl->icount[g]);
+        }
+      }
+    }
+  }
+}
+
+// All chunks of a split row get the OR of their masks (the row's activity
+// needs every chunk), and become work items.  Warp per split row.
+__global__ void __launch_bounds__(kThreads) k_bmark_split(DevMatrix M, BatchState S) {
+  BCtrl *ctrl = S.ctrl;
+  const BParams P = load_params(ctrl);
+  if (P.err) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nslots = S.nslots;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < M.nsplit_rows; s += nw) {
+    const int32_t q0 = M.split_cbeg[s], q1 = M.split_cbeg[s + 1];
+    for (int gq = 0; gq < P.Gs; gq += 4) {
+      uint4 m = make_uint4(0u, 0u, 0u, 0u);
+      for (int32_t q = q0 + lane; q < q1; q += 32)
+        m = or4(m, *reinterpret_cast<const uint4 *>(S.cmask + (int64_t)M.split_cidx[q] * P.Gs + gq));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        m.x |= __shfl_xor_sync(kFull, m.x, o);
+        m.y |= __shfl_xor_sync(kFull, m.y, o);
+        m.z |= __shfl_xor_sync(kFull, m.z, o);
+        m.w |= __shfl_xor_sync(kFull, m.w, o);
+      }
+      for (int32_t q = q0 + lane; q < q1; q += 32)
+        *reinterpret_cast<uint4 *>(S.cmask + (int64_t)M.split_cidx[q] * P.Gs + gq) = m;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int g = gq + u;
+        if (g >= P.G || word4(m, u) == 0u) continue;  // uniform
+        for (int32_t qb = q0; qb < q1; qb += 32) {
+          const int32_t q = qb + lane;
+          warp_append<int32_t>(q < q1, q < q1 ? M.split_cidx[q] : 0,
+                               S.items + (int64_t)g * nslots, &ctrl->icount[g]);
+        }
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------------- k_bact --
+
+__global__ void __launch_bounds__(kActWarps * 32, 3) k_bact(DevMatrix M, BatchState S) {
+  BCtrl *ctrl = S.ctrl;
+  const BParams P = load_params(ctrl);
+  if (P.err) return;
+  const int p = P.round & 1;
+  const int lane = threadIdx.x & 31;
+  // regions of the work list: lane g holds the item count of group g
+  const int cnt = lane < P.G ? ctrl->icount[lane] : 0;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - cnt;
+  const int64_t split_slots = (int64_t)M.nslices_split * kSliceW;
+  const int nw = gridDim.x * kActWarps;
+  __shared__ uint32_t s_stage[kActWarps][kStage];
+  __shared__ PairBuf s_pairs[kActWarps];
+  DirtyStage st{s_stage[threadIdx.x >> 5], 0};
+  PairQueue pq{&s_pairs[threadIdx.x >> 5], 0};
+  for (int it = blockIdx.x * kActWarps + (threadIdx.x >> 5); it < total; it += nw) {
+    const int g = __popc(__ballot_sync(kFull, lane < P.G && it >= incl));
+    const int off = __shfl_sync(kFull, excl, g);
+    const int64_t cs = S.items[(int64_t)g * S.nslots + (it - off)];
+    const int node = g * 32 + lane;
+    const uint32_t mask = S.cmask[cs * P.Gs + g];
+    const bool on = ((mask >> lane) & 1u) != 0u;
+    const int32_t row = M.chunk_row[cs];
+    const int32_t lenf = M.chunk_len[cs];
+    const int len = lenf & kLenMask;
+    const bool exact = (lenf & kExactFlag) != 0;
+    const int64_t base = M.slice_off[cs / kSliceW] + (cs % kSliceW);
+    const double lhs = S.lhs[row], rhs = S.rhs[row];
+    const bool need_min = d_isfinite(rhs), need_max = d_isfinite(lhs);
+    const BAct r = chunk_activity(M, S, base, len, node, need_min, need_max, !exact, P);
+    if (cs < split_slots) {
+      BPartial pt;
+      pt.minfin = r.minfin;
+      pt.maxfin = r.maxfin;
+      pt.mininf = r.mininf;
+      pt.maxinf = r.maxinf;
+      pt.tr = r.tr;
+      pt.tl = r.tl;
+      S.part[cs * P.Bp + node] = pt;
+      continue;
+    }
+    RowView rv;
+    rv.minfin = r.minfin;
+    rv.maxfin = r.maxfin;
+    rv.lhs = lhs;
+    rv.rhs = rhs;
+    rv.mininf = r.mininf;
+    rv.maxinf = r.maxinf;
+    rv.exact = exact ? 1 : 0;
+    const bool infeas = row_sides_eval(rv, r.tr, r.tl, P.eps_feas);
+    note_nodes(S.inf_bits, g, on && infeas);
+    const bool go = on && rv.act != 0;
+    if (!__any_sync(kFull, go)) continue;
+    chunk_candidates(M, S, base, len, node, go, row, rv, P, pq, st, S.dirty[p],
+                     &ctrl->ndirty[p]);
+  }
+  drain_pairs(pq, M, S, P, st, S.dirty[p], &ctrl->ndirty[p]);
+}
+
+// ---------------------------------------------------------- split rows --
+
+__global__ void __launch_bounds__(kThreads) k_bcombine(DevMatrix M, BatchState S) {
+  const BParams P = load_params(S.ctrl);
+  if (P.err) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t pairs = (int64_t)M.nsplit_rows * P.G;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < pairs; w += nw) {
+    const int s = (int)(w / P.G), g = (int)(w % P.G);
+    const int32_t q0 = M.split_cbeg[s], q1 = M.split_cbeg[s + 1];
+    const int64_t c0 = M.split_cidx[q0];
+    const uint32_t mask = S.cmask[c0 * P.Gs + g];
+    if (mask == 0u) {
+      if (lane == 0) S.srow_act[(int64_t)s * P.Gs + g] = 0u;
+      continue;
+    }
+    const int node = g * 32 + lane;
+    const bool on = ((mask >> lane) & 1u) != 0u;
+    const int32_t row = M.split_row[s];
+    RowView rv;
+    rv.minfin = rv.maxfin = 0.0;
+    rv.mininf = rv.maxinf = 0;
+    float tr = -f_inf(), tl = -f_inf();
+    for (int32_t q = q0; q < q1; ++q) {  // the row's pieces in order
+      const BPartial pt = S.part[(int64_t)M.split_cidx[q] * P.Bp + node];
+      rv.minfin += pt.minfin;
+      rv.maxfin += pt.maxfin;
+      rv.mininf += pt.mininf;
+      rv.maxinf += pt.maxinf;
+      tr = fmaxf(tr, pt.tr);
+      tl = fmaxf(tl, pt.tl);
+    }
+    rv.lhs = S.lhs[row];
+    rv.rhs = S.rhs[row];
+    rv.exact = (M.chunk_len[c0] & kExactFlag) ? 1 : 0;
+    const bool infeas = row_sides_eval(rv, tr, tl, P.eps_feas);
+    note_nodes(S.inf_bits, g, on && infeas);
+    BRowTot t;
+    t.minfin = rv.minfin;
+    t.maxfin = rv.maxfin;
+    t.mininf = rv.mininf;
+    t.maxinf = rv.maxinf;
+    t.thr_r = rv.thr_r;
+    t.thr_l = rv.thr_l;
+    S.rowtot[(int64_t)s * P.Bp + node] = t;
+    const unsigned act = __ballot_sync(kFull, on && rv.act != 0);
+    if (lane == 0) S.srow_act[(int64_t)s * P.Gs + g] = act;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchState S) {
+  BCtrl *ctrl = S.ctrl;
+  const BParams P = load_params(ctrl);
+  if (P.err) return;
+  const int p = P.round & 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t pairs = (int64_t)M.nslices_split * kSliceW * P.G;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  __shared__ uint32_t s_stage[kThreads / 32][kStage];
+  __shared__ PairBuf s_pairs[kThreads / 32];
+  DirtyStage st{s_stage[threadIdx.x >> 5], 0};
+  PairQueue pq{&s_pairs[threadIdx.x >> 5], 0};
+  for (int64_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < pairs; w += nw) {
+    const int64_t cs = w / P.G;
+    const int g = (int)(w % P.G);
+    const int32_t s = M.chunk_sidx[cs];
+    if (s < 0) continue;
+    const uint32_t act = S.srow_act[(int64_t)s * P.Gs + g];
+    if (act == 0u) continue;
+    const int node = g * 32 + lane;
+    const bool on = ((act >> lane) & 1u) != 0u;
+    const int32_t row = M.chunk_row[cs];
+    const int32_t lenf = M.chunk_len[cs];
+    const BRowTot t = S.rowtot[(int64_t)s * P.Bp + node];
+    RowView rv;
+    rv.minfin = t.minfin;
+    rv.maxfin = t.maxfin;
+    rv.lhs = S.lhs[row];
+    rv.rhs = S.rhs[row];
+    rv.mininf = t.mininf;
+    rv.maxinf = t.maxinf;
+    rv.thr_r = t.thr_r;
+    rv.thr_l = t.thr_l;
+    rv.exact = (lenf & kExactFlag) ? 1 : 0;
+    rv.act = on ? 1 : 0;
+    const int64_t base = M.slice_off[cs / kSliceW] + (cs % kSliceW);
+    chunk_candidates(M, S, base, lenf & kLenMask, node, on, row, rv, P, pq, st, S.dirty[p],
+                     &ctrl->ndirty[p]);
+  }
+  drain_pairs(pq, M, S, P, st, S.dirty[p], &ctrl->ndirty[p]);
+}
+
+// ----------------------------------------------------------- k_bfinish --
+
+// Commits the entries improved this round (the next state becomes the
+// current one), tests them for crossing bounds (Sec. 1.1, remark after
+// Step 3), and records which (variable, node) pairs changed; clears the
+// change masks of the previous round.  The last block to arrive counts the
+// round for every live node, ends the nodes that stopped (no change,
+// infeasible, or the cap) and sets the WHILE condition.
+__global__ void __launch_bounds__(kThreads)
+k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_cond) {
+  BCtrl *ctrl = S.ctrl;
+  const BParams P = load_params(ctrl);
+  const int p = P.round & 1;
+  const int lane = threadIdx.x & 31;
+  __shared__ uint32_t s_chg[kMaxGroups], s_inf[kMaxGroups];
+  __shared__ int s_last;
+  if (threadIdx.x < kMaxGroups) {
+    s_chg[threadIdx.x] = 0u;
+    s_inf[threadIdx.x] = 0u;
+  }
+  __syncthreads();
+  if (!P.err) {
+    const int32_t nd = ctrl->ndirty[p];
+    const uint32_t *list = S.dirty[p];
+    uint32_t *chg_next = S.chg[p ^ 1];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count: lanes of one warp merge their change-mask
+    // updates of the same (variable, group) word into one atomic
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nd;
+         i0 += stride) {
+      const int64_t i = i0 + lane;
+      const bool valid = i < nd;
+      unsigned long long widx = ~0ull;
+      uint32_t bit = 0u;
+      if (valid) {
+        const uint32_t e = list[i];
+        const uint32_t j = e / (uint32_t)P.Bp, node = e % (uint32_t)P.Bp;
+        const longlong2 kk = reinterpret_cast<const longlong2 *>(S.nkey)[e];
+        const double L = val_of_key(kk.x), U = val_of_key(kk.y);
+        S.cur[e] = make_double2(L, U);
+        if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
+          const bool cross = S.vt[j] ? (L > U) : (L > U + P.eps_feas * fmax(1.0, fabs(U)));
+          if (cross) atomicOr(&s_inf[node >> 5], 1u << (node & 31));
+        }
+        widx = (unsigned long long)j * P.Gs + (node >> 5);
+        bit = 1u << (node & 31);
+        atomicOr(&s_chg[node >> 5], bit);
+      }
+      const unsigned peers = __match_any_sync(kFull, widx);
+      const uint32_t bits = __reduce_or_sync(peers, bit);
+      if (valid && lane == __ffs(peers) - 1) atomicOr(&chg_next[widx], bits);
+    }
+    // clear the change masks that the previous round's entries set
+    const int32_t np = ctrl->ndirty[p ^ 1];
+    const uint32_t *prev = S.dirty[p ^ 1];
+    uint32_t *chg_cur = S.chg[p];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
+      const uint32_t e = prev[i];
+      const uint32_t j = e / (uint32_t)P.Bp, node = e % (uint32_t)P.Bp;
+      chg_cur[(int64_t)j * P.Gs + (node >> 5)] = 0u;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < P.G) {
+    if (s_chg[threadIdx.x]) atomicOr(&S.chg_bits[threadIdx.x], s_chg[threadIdx.x]);
+    if (s_inf[threadIdx.x]) atomicOr(&S.inf_bits[threadIdx.x], s_inf[threadIdx.x]);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int32_t r = P.round + 1;
+  const volatile uint32_t *chg_bits = S.chg_bits;
+  const volatile uint32_t *inf_bits = S.inf_bits;
+  for (int node = threadIdx.x; node < P.Bp; node += blockDim.x) {
+    int32_t d = S.node_done[node];
+    if (!d && !P.err) {
+      const uint32_t b = 1u << (node & 31);
+      S.node_rounds[node] = r;
+      if (inf_bits[node >> 5] & b) d = 1;
+      else if (!(chg_bits[node >> 5] & b)) d = 1;
+      else if (r >= P.max_rounds) {
+        d = 1;
+        S.node_status[node] = 1;
+      }
+    }
+    S.node_done[node] = d;
+  }
+  __syncthreads();
+  int live = 0;
+  for (int g = threadIdx.x; g < P.Gs; g += blockDim.x) {
+    uint32_t w = 0u;
+    if (g < P.G)
+      for (int b = 0; b < 32; ++b)
+        if (!S.node_done[g * 32 + b]) w |= 1u << b;
+    S.alive[g] = w;
+    live |= w != 0u;
+  }
+  live = __syncthreads_or(live);
+  if (threadIdx.x < kMaxGroups) {
+    ctrl->icount[threadIdx.x] = 0;
+    S.chg_bits[threadIdx.x] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    volatile BCtrl *vc = ctrl;
+    vc->round = r;
+    const int32_t cont = (live && !P.err) ? 1 : 0;
+    vc->any_alive = cont;
+    vc->ndirty[p ^ 1] = 0;
+    vc->blocks_done = 0;
+    __threadfence();
+    if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
+  }
+}
+
+// ---------------------------------------------------- prologue/epilogue --
+
+// Normalises node-major bounds (lb[node*n + j]) into the node-minor state,
+// 32 variables x 32 nodes per tile through shared memory so that both the
+// reads and the writes are coalesced.  |v| >= thr becomes +-inf, integer
+// bounds are rounded (ceil(lb - eps_int), floor(ub + eps_int)); NaN and
+// contradictory infinities set ctrl->err.  Padding nodes get [0, 0].
+__global__ void __launch_bounds__(kThreads)
+k_bprologue_bounds(BatchState S, int32_t n, int32_t count, int32_t Bp, const double *lb,
+                   const double *ub, const uint8_t *vartype, double eps_int, double eps_feas,
+                   double thr) {
+  __shared__ double sL[32][33], sU[32][33];
+  const double pinf = __longlong_as_double(0x7FF0000000000000ll);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int G = Bp / 32;
+  const int64_t tiles_x = ((int64_t)n + 31) / 32;
+  const int64_t tiles = tiles_x * G;
+  bool bad = false;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t j0 = (t % tiles_x) * 32;
+    const int g = (int)(t / tiles_x);
+    for (int yy = ty; yy < 32; yy += kThreads / 32) {
+      const int node = g * 32 + yy;
+      const int64_t j = j0 + tx;
+      double L = 0.0, U = 0.0;
+      if (node < count && j < n) {
+        L = lb[(int64_t)node * n + j];
+        U = ub[(int64_t)node * n + j];
+        if (d_isnan(L) || d_isnan(U) || L >= thr || U <= -thr) {
+          bad = true;
+          L = 0.0;
+          U = 0.0;
+        }
+        if (L <= -thr) L = -pinf;
+        if (U >= thr) U = pinf;
+        const bool isint = vartype[j] != 0;
+        if (isint) {
+          if (d_isfinite(L)) L = ceil(L - eps_int);
+          if (d_isfinite(U)) U = floor(U + eps_int);
+        }
+        // Bounds that already cross: the crossing test of round 1 covers
+        // every variable, and tightening cannot undo a crossing, so the
+        // node is flagged now and ends after its first round.
+        if (L > U && (isint || L > U + eps_feas * fmax(1.0, fabs(U))))
+          atomicOr(&S.inf_bits[node >> 5], 1u << (node & 31));
+      }
+      sL[yy][tx] = L;
+      sU[yy][tx] = U;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += kThreads / 32) {
+      const int64_t j = j0 + yy;
+      if (j < n) {
+        const int64_t e = j * Bp + g * 32 + tx;
+        const double L = sL[tx][yy], U = sU[tx][yy];
+        S.cur[e] = make_double2(L, U);
+        reinterpret_cast<longlong2 *>(S.nkey)[e] = make_longlong2(key_of(L), key_of(U));
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) atomicExch(&S.ctrl->err, DP_ERR_NAN_INPUT);
+}
+
+// Variable types, normalised sides, per-node state and the live masks.
+__global__ void k_bprologue_misc(BatchState S, int32_t m, int32_t n, int32_t count, int32_t Bp,
+                                 const uint8_t *vartype, const double *lhs, const double *rhs,
+                                 double thr) {
+  const double pinf = __longlong_as_double(0x7FF0000000000000ll);
+  const int Gs = ((Bp / 32) + 3) & ~3;
+  int64_t total = n > m ? n : m;
+  if (total < Bp) total = Bp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) S.vt[i] = vartype[i] ? 1 : 0;
+    if (i < m) {
+      double l = lhs[i], r = rhs[i];
+      if (d_isnan(l) || d_isnan(r) || l >= thr || r <= -thr) {
+        atomicExch(&S.ctrl->err, DP_ERR_NAN_INPUT);
+        l = 0.0;
+        r = 0.0;
+      }
+      if (l <= -thr) l = -pinf;
+      if (r >= thr) r = pinf;
+      S.lhs[i] = l;
+      S.rhs[i] = r;
+    }
+    if (i < kMaxGroups) {
+      S.inf_bits[i] = 0u;
+      S.chg_bits[i] = 0u;
+    }
+    if (i < Bp) {
+      S.node_rounds[i] = 0;
+      S.node_status[i] = 0;
+      S.node_done[i] = i < count ? 0 : 1;
+    }
+    if (i < Gs) {
+      const int64_t lo = i * 32;
+      uint32_t w = 0u;
+      for (int b = 0; b < 32; ++b)
+        if (lo + b < count) w |= 1u << b;
+      S.alive[i] = w;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bepilogue(BatchState S, int32_t n, int32_t count, int32_t Bp, double *lb_out,
+            double *ub_out) {
+  __shared__ double sL[32][33], sU[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int G = Bp / 32;
+  const int64_t tiles_x = ((int64_t)n + 31) / 32;
+  const int64_t tiles = tiles_x * G;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t j0 = (t % tiles_x) * 32;
+    const int g = (int)(t / tiles_x);
+    for (int yy = ty; yy < 32; yy += kThreads / 32) {
+      const int64_t j = j0 + yy;
+      double2 b = make_double2(0.0, 0.0);
+      if (j < n) b = S.cur[j * Bp + g * 32 + tx];
+      sL[tx][yy] = b.x;
+      sU[tx][yy] = b.y;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += kThreads / 32) {
+      const int node = g * 32 + yy;
+      const int64_t j = j0 + tx;
+      if (node < count && j < n) {
+        lb_out[(int64_t)node * n + j] = sL[yy][tx];
+        ub_out[(int64_t)node * n + j] = sU[yy][tx];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int grid_for(int64_t work, int threads, int max_blocks) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_batch_prologue(const DevMatrix &M, const BatchState &S, int32_t count,
+                                  const double *lb, const double *ub, const uint8_t *vartype,
+                                  const double *lhs, const double *rhs, double eps_int,
+                                  double eps_feas, double thr, int num_sms, cudaStream_t st) {
+  const int32_t Bp = (count + 31) / 32 * 32;
+  const int64_t tiles = (((int64_t)M.n + 31) / 32) * (Bp / 32);
+  int64_t total = M.n > M.m ? M.n : M.m;
+  if (total < Bp) total = Bp;
+  k_bprologue_misc<<<grid_for(total, kThreads, num_sms * 16), kThreads, 0, st>>>(
+      S, M.m, M.n, count, Bp, vartype, lhs, rhs, thr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || M.n == 0) return e;
+  int nb = (int)(tiles < (int64_t)num_sms * 16 ? tiles : (int64_t)num_sms * 16);
+  k_bprologue_bounds<<<nb, kThreads, 0, st>>>(S, M.n, count, Bp, lb, ub, vartype, eps_int,
+                                              eps_feas, thr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_epilogue(const DevMatrix &M, const BatchState &S, int32_t count,
+                                  double *lb_out, double *ub_out, int num_sms,
+                                  cudaStream_t st) {
+  if (M.n == 0 || count == 0) return cudaSuccess;
+  const int32_t Bp = (count + 31) / 32 * 32;
+  const int64_t tiles = (((int64_t)M.n + 31) / 32) * (Bp / 32);
+  int nb = (int)(tiles < (int64_t)num_sms * 16 ? tiles : (int64_t)num_sms * 16);
+  k_bepilogue<<<nb, kThreads, 0, st>>>(S, M.n, count, Bp, lb_out, ub_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
+                               cudaGraphConditionalHandle handle, int use_cond, int num_sms,
+                               cudaStream_t st, cudaEvent_t *ev) {
+  cudaError_t e;
+  const int64_t nslots = (int64_t)M.nslices * kSliceW;
+  const bool split = M.nsplit_rows > 0;
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], st);
+  };
+  mark(0);
+  k_bmark<<<grid_for(nslots, kThreads, num_sms * 8), kThreads, 0, st>>>(M, S);
+  mark(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mark(2);
+  if (split)
+    k_bmark_split<<<grid_for((int64_t)M.nsplit_rows * 32, kThreads, num_sms * 4), kThreads, 0,
+                    st>>>(M, S);
+  mark(3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mark(4);
+  k_bact<<<num_sms * 3, kActWarps * 32, 0, st>>>(M, S);
+  mark(5);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mark(6);
+  if (split) k_bcombine<<<num_sms * 4, kThreads, 0, st>>>(M, S);
+  mark(7);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mark(8);
+  if (split) k_bcand_split<<<num_sms * 3, kThreads, 0, st>>>(M, S);
+  mark(9);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mark(10);
+  k_bfinish<<<num_sms * 4, kThreads, 0, st>>>(S, M.n, handle, use_cond);
+  mark(11);
+  return cudaGetLastError();
+}
+
+}  // namespace dp

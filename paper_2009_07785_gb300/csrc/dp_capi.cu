@@ -41,6 +41,23 @@ struct dp_matrix {
   // the round loop
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // batched nodes (allocated on the first dp_propagate_nodes call)
+  struct BatchWs *batch = nullptr;
+};
+
+// Workspace of dp_propagate_nodes for up to Bp_cap nodes per launch.
+struct BatchWs {
+  int32_t Bp_cap = 0;
+  std::vector<void *> allocs;
+  dp::BatchState S{};
+  dp::BCtrl *h_ctrl = nullptr;  // pinned
+  int32_t *h_nodes = nullptr;   // pinned [3*Bp_cap]: infeasible, rounds, status
+  // staging of host inputs / outputs, allocated when first needed
+  double *st_lb = nullptr, *st_ub = nullptr, *out_lb = nullptr, *out_ub = nullptr;
+  double *st_lhs = nullptr, *st_rhs = nullptr;
+  uint8_t *st_vt = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -84,10 +101,11 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Makes the round-loop graph of a matrix: one WHILE node whose body is the
-// round's kernels; the condition starts at 1 on every launch.
-int build_graph(dp_matrix *mat) {
-  dp_ctx *ctx = mat->ctx;
+// Makes a round-loop graph: one WHILE node whose body is the kernels that
+// `body(handle, stream)` launches; the condition starts at 1 on every launch
+// and the last kernel of the body sets it on the device.
+template <typename Body>
+int build_loop_graph(Body body, cudaGraph_t *graph_out, cudaGraphExec_t *exec_out) {
   cudaGraph_t g = nullptr;
   CUDA_TRY(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle h;
@@ -104,16 +122,16 @@ int build_graph(dp_matrix *mat) {
     cudaGraphDestroy(g);
     return DP_ERR_CUDA;
   }
-  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
   cudaStream_t cs = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGraphDestroy(g);
     return DP_ERR_CUDA;
   }
-  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0,
                                                 cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    cudaError_t le = dp::launch_round_body(mat->M, mat->S, mat->vt_ws, h, ctx->num_sms, cs);
+    cudaError_t le = body(h, cs);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
     if (le != cudaSuccess) e = le;
@@ -130,9 +148,18 @@ int build_graph(dp_matrix *mat) {
     cudaGraphDestroy(g);
     return DP_ERR_CUDA;
   }
-  mat->graph = g;
-  mat->exec = ex;
+  *graph_out = g;
+  *exec_out = ex;
   return DP_OK;
+}
+
+int build_graph(dp_matrix *mat) {
+  const int sms = mat->ctx->num_sms;
+  return build_loop_graph(
+      [mat, sms](cudaGraphConditionalHandle h, cudaStream_t cs) {
+        return dp::launch_round_body(mat->M, mat->S, mat->vt_ws, h, sms, cs);
+      },
+      &mat->graph, &mat->exec);
 }
 
 }  // namespace
@@ -207,10 +234,23 @@ void dp_destroy(dp_ctx *ctx) {
   delete ctx;
 }
 
+namespace {
+void free_batch(BatchWs *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void *p : b->allocs) cudaFree(p);
+  if (b->h_ctrl) cudaFreeHost(b->h_ctrl);
+  if (b->h_nodes) cudaFreeHost(b->h_nodes);
+  delete b;
+}
+}  // namespace
+
 void dp_matrix_free(dp_matrix *mat) {
   if (!mat) return;
   cudaSetDevice(mat->ctx->device);
   cudaStreamSynchronize(mat->ctx->stream);
+  free_batch(mat->batch);
   if (mat->exec) cudaGraphExecDestroy(mat->exec);
   if (mat->graph) cudaGraphDestroy(mat->graph);
   for (void *p : mat->allocs) cudaFree(p);
@@ -451,3 +491,289 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ batched B&B nodes --
+
+namespace {
+
+template <typename T>
+int batch_alloc(BatchWs *b, T **p, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * (count > 0 ? count : 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA;
+  }
+  b->allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return DP_OK;
+}
+
+// Largest node count of one launch for this matrix: a multiple of 32, at
+// most 32*kMaxGroups, and small enough that entry indices (j*Bp + node,
+// 32-bit) and list counts (2*n*Bp dirty entries, G*slots work items) fit in
+// a signed 32-bit integer.
+int32_t batch_slab(const dp_matrix *mat) {
+  const int64_t n = mat->M.n > 0 ? mat->M.n : 1;
+  const int64_t slots = (int64_t)mat->M.nslices * dp::kSliceW > 0
+                            ? (int64_t)mat->M.nslices * dp::kSliceW : 1;
+  int64_t bp = 32 * dp::kMaxGroups;
+  const int64_t lim = (int64_t(1) << 30) - 1;
+  while (bp >= 32 && (n * bp > lim || slots * (bp / 32) > lim)) bp -= 32;
+  return (int32_t)bp;
+}
+
+// Makes (or reuses) the workspace for Bp nodes per launch.
+int ensure_batch(dp_matrix *mat, int32_t Bp) {
+  if (mat->batch && mat->batch->Bp_cap >= Bp) return DP_OK;
+  if (mat->batch) {
+    cudaStreamSynchronize(mat->ctx->stream);
+    free_batch(mat->batch);
+    mat->batch = nullptr;
+  }
+  BatchWs *b = new (std::nothrow) BatchWs();
+  if (!b) return DP_ERR_OOM;
+  const dp::DevMatrix &M = mat->M;
+  const size_t n = (size_t)M.n, m = (size_t)M.m;
+  const size_t G = (size_t)Bp / 32, Gs = (G + 3) & ~(size_t)3;
+  const size_t nslots = (size_t)M.nslices * dp::kSliceW;
+  const size_t split_slots = (size_t)M.nslices_split * dp::kSliceW;
+  const size_t srows = (size_t)M.nsplit_rows;
+  dp::BatchState &S = b->S;
+  int rc = DP_OK;
+#define BTRY(x)                 \
+  do {                          \
+    if ((rc = (x)) != DP_OK) {  \
+      free_batch(b);            \
+      return rc;                \
+    }                           \
+  } while (0)
+  BTRY(batch_alloc(b, &S.cur, n * Bp));
+  BTRY(batch_alloc(b, &S.nkey, 2 * n * Bp));
+  BTRY(batch_alloc(b, &S.chg[0], n * Gs));
+  BTRY(batch_alloc(b, &S.chg[1], n * Gs));
+  BTRY(batch_alloc(b, &S.dirty[0], 2 * n * Bp));
+  BTRY(batch_alloc(b, &S.dirty[1], 2 * n * Bp));
+  BTRY(batch_alloc(b, &S.cmask, nslots * Gs));
+  BTRY(batch_alloc(b, &S.items, G * nslots));
+  BTRY(batch_alloc(b, &S.part, split_slots * Bp));
+  BTRY(batch_alloc(b, &S.rowtot, srows * Bp));
+  BTRY(batch_alloc(b, &S.srow_act, srows * Gs));
+  BTRY(batch_alloc(b, &S.inf_bits, (size_t)dp::kMaxGroups));
+  BTRY(batch_alloc(b, &S.chg_bits, (size_t)dp::kMaxGroups));
+  BTRY(batch_alloc(b, &S.node_rounds, (size_t)Bp));
+  BTRY(batch_alloc(b, &S.node_status, (size_t)Bp));
+  BTRY(batch_alloc(b, &S.node_done, (size_t)Bp));
+  BTRY(batch_alloc(b, &S.alive, (size_t)dp::kMaxGroups));
+  BTRY(batch_alloc(b, &S.lhs, m));
+  BTRY(batch_alloc(b, &S.rhs, m));
+  BTRY(batch_alloc(b, &S.vt, n));
+  BTRY(batch_alloc(b, &S.ctrl, 1));
+  S.nslots = (int64_t)nslots;
+  if (cudaMallocHost(&b->h_ctrl, sizeof(dp::BCtrl)) != cudaSuccess ||
+      cudaMallocHost(&b->h_nodes, sizeof(int32_t) * 3 * (size_t)Bp) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return DP_ERR_OOM;
+  }
+  b->Bp_cap = Bp;
+  const int sms = mat->ctx->num_sms;
+  const dp::DevMatrix Mc = mat->M;
+  const dp::BatchState Sc = b->S;
+  BTRY(build_loop_graph(
+      [Mc, Sc, sms](cudaGraphConditionalHandle h, cudaStream_t cs) {
+        return dp::launch_batch_round(Mc, Sc, h, 1, sms, cs, nullptr);
+      },
+      &b->graph, &b->exec));
+#undef BTRY
+  mat->batch = b;
+  return DP_OK;
+}
+
+// Device copy of a host input (staged), or the device pointer itself.
+// The staging buffer holds `cap` elements (allocated on first use).
+template <typename T>
+int stage_in(BatchWs *b, T **slot, const T *src, size_t count, size_t cap, cudaStream_t st,
+             const T **out) {
+  if (count == 0 || is_device_ptr(src)) {
+    *out = src;
+    return DP_OK;
+  }
+  if (!*slot) {
+    int rc = batch_alloc(b, slot, cap);
+    if (rc) return rc;
+  }
+  CUDA_TRY(cudaMemcpyAsync(*slot, src, sizeof(T) * count, cudaMemcpyHostToDevice, st));
+  *out = *slot;
+  return DP_OK;
+}
+
+constexpr int kBatchStages = 6;  // mark, mark_split, act, combine, cand_split, finish
+
+int batch_hostloop(dp_matrix *mat, BatchWs *b, int32_t max_rounds, float *kernel_ms,
+                   int32_t *kernel_launches) {
+  dp_ctx *ctx = mat->ctx;
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t ev[2 * kBatchStages] = {};
+  const bool timed = kernel_ms != nullptr;
+  if (timed)
+    for (int i = 0; i < 2 * kBatchStages; ++i)
+      if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+        for (int q = 0; q < i; ++q) cudaEventDestroy(ev[q]);
+        return DP_ERR_CUDA;
+      }
+  const bool split = mat->M.nsplit_rows > 0;
+  const bool launched[kBatchStages] = {true, split, true, split, split, true};
+  int status = DP_OK;
+  for (int32_t r = 0; r < max_rounds; ++r) {
+    cudaError_t e = dp::launch_batch_round(mat->M, b->S, 0, 0, ctx->num_sms, st,
+                                           timed ? ev : nullptr);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->h_ctrl, b->S.ctrl, sizeof(dp::BCtrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      status = DP_ERR_CUDA;
+      break;
+    }
+    for (int k = 0; k < kBatchStages; ++k) {
+      if (!launched[k]) continue;
+      if (kernel_launches) kernel_launches[k] += 1;
+      float t;
+      if (timed && cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]) == cudaSuccess)
+        kernel_ms[k] += t;
+    }
+    if (b->h_ctrl->err || !b->h_ctrl->any_alive) break;
+  }
+  if (timed)
+    for (int i = 0; i < 2 * kBatchStages; ++i) cudaEventDestroy(ev[i]);
+  return status;
+}
+
+// One dp_propagate_nodes call.  With `hostloop` the rounds are driven from
+// the host (one synchronisation per round) so that each stage can be timed
+// with CUDA events; the results are the same.
+int nodes_call(dp_ctx *ctx, const dp_matrix *cmat, int32_t count, const double *lb,
+               const double *ub, const uint8_t *vartype, const double *lhs, const double *rhs,
+               const dp_params *params, double *lb_out, double *ub_out, int32_t *infeasible,
+               int32_t *rounds, int32_t *status, bool hostloop, float *kernel_ms,
+               int32_t *kernel_launches) {
+  if (!ctx || !cmat || count < 0) return DP_ERR_INVALID_ARG;
+  if (cmat->ctx != ctx) return DP_ERR_INVALID_ARG;
+  if (count == 0) return DP_OK;
+  if (!infeasible || !rounds) return DP_ERR_INVALID_ARG;
+  dp_matrix *mat = const_cast<dp_matrix *>(cmat);
+  const int32_t m = mat->M.m, n = mat->M.n;
+  if (n > 0 && (!lb || !ub || !vartype || !lb_out || !ub_out)) return DP_ERR_INVALID_ARG;
+  if (m > 0 && (!lhs || !rhs)) return DP_ERR_INVALID_ARG;
+  dp_params p;
+  if (params) p = *params; else dp_params_default(&p);
+  if (p.max_rounds < 0 || !(p.eps_int >= 0) || !(p.tau_rel >= 0) || !(p.eps_feas >= 0) ||
+      !(p.inf_threshold > 0))
+    return DP_ERR_INVALID_ARG;
+  const int32_t slab = batch_slab(mat);
+  if (slab < 32) return DP_ERR_INVALID_ARG;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  {
+    const int32_t want = count < slab ? (count + 31) / 32 * 32 : slab;
+    int rc = ensure_batch(mat, want);
+    if (rc) return rc;
+  }
+  BatchWs *b = mat->batch;
+  const int32_t per = count < b->Bp_cap ? count : b->Bp_cap;
+  const uint8_t *d_vt = nullptr;
+  const double *d_lhs = nullptr, *d_rhs = nullptr;
+  int rc;
+  if ((rc = stage_in(b, &b->st_vt, vartype, (size_t)n, (size_t)n, st, &d_vt))) return rc;
+  if ((rc = stage_in(b, &b->st_lhs, lhs, (size_t)m, (size_t)m, st, &d_lhs))) return rc;
+  if ((rc = stage_in(b, &b->st_rhs, rhs, (size_t)m, (size_t)m, st, &d_rhs))) return rc;
+  const bool host_out = n > 0 && !(is_device_ptr(lb_out) && is_device_ptr(ub_out));
+  const size_t cap = (size_t)b->Bp_cap * (size_t)n;
+  if (host_out && !b->out_lb) {
+    if ((rc = batch_alloc(b, &b->out_lb, cap))) return rc;
+    if ((rc = batch_alloc(b, &b->out_ub, cap))) return rc;
+  }
+  bool any_cap = false;
+  for (int32_t s0 = 0; s0 < count; s0 += per) {
+    const int32_t cnt = count - s0 < per ? count - s0 : per;
+    const int32_t Bp = (cnt + 31) / 32 * 32;
+    const size_t off = (size_t)s0 * (size_t)n, len = (size_t)cnt * (size_t)n;
+    const double *d_lb = nullptr, *d_ub = nullptr;
+    if ((rc = stage_in(b, &b->st_lb, n > 0 ? lb + off : lb, len, cap, st, &d_lb))) return rc;
+    if ((rc = stage_in(b, &b->st_ub, n > 0 ? ub + off : ub, len, cap, st, &d_ub))) return rc;
+    dp::BCtrl *hc = b->h_ctrl;
+    std::memset(hc, 0, sizeof(*hc));
+    hc->max_rounds = p.max_rounds;
+    hc->B = cnt;
+    hc->Bp = Bp;
+    hc->G = Bp / 32;
+    hc->any_alive = 1;
+    hc->eps_int = p.eps_int;
+    hc->tau_rel = p.tau_rel;
+    hc->eps_feas = p.eps_feas;
+    hc->inf_thr = p.inf_threshold;
+    const size_t Gs = (size_t)((Bp / 32 + 3) & ~3);
+    CUDA_TRY(cudaMemcpyAsync(b->S.ctrl, hc, sizeof(*hc), cudaMemcpyHostToDevice, st));
+    if (n > 0) {
+      CUDA_TRY(cudaMemsetAsync(b->S.chg[0], 0, sizeof(uint32_t) * Gs * n, st));
+      CUDA_TRY(cudaMemsetAsync(b->S.chg[1], 0, sizeof(uint32_t) * Gs * n, st));
+    }
+    CUDA_TRY(dp::launch_batch_prologue(mat->M, b->S, cnt, d_lb, d_ub, d_vt, d_lhs, d_rhs,
+                                       p.eps_int, p.eps_feas, p.inf_threshold, ctx->num_sms, st));
+    if (p.max_rounds > 0 && !hostloop) CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    if (p.max_rounds > 0 && hostloop) {
+      int r2 = batch_hostloop(mat, b, p.max_rounds, kernel_ms, kernel_launches);
+      if (r2) return r2;
+    }
+    if (n > 0) {
+      double *o_lb = host_out ? b->out_lb : lb_out + off;
+      double *o_ub = host_out ? b->out_ub : ub_out + off;
+      CUDA_TRY(dp::launch_batch_epilogue(mat->M, b->S, cnt, o_lb, o_ub, ctx->num_sms, st));
+      if (host_out) {
+        CUDA_TRY(cudaMemcpyAsync(lb_out + off, o_lb, 8 * len, cudaMemcpyDefault, st));
+        CUDA_TRY(cudaMemcpyAsync(ub_out + off, o_ub, 8 * len, cudaMemcpyDefault, st));
+      }
+    }
+    int32_t *hn = b->h_nodes;
+    CUDA_TRY(cudaMemcpyAsync(hn, b->S.inf_bits, 4 * (size_t)dp::kMaxGroups, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hn + Bp, b->S.node_rounds, 4 * (size_t)cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hn + 2 * Bp, b->S.node_status, 4 * (size_t)cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hc, b->S.ctrl, sizeof(*hc), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (hc->err) return hc->err;
+    for (int32_t i = 0; i < cnt; ++i) {
+      infeasible[s0 + i] = (int32_t)(((uint32_t)hn[i >> 5] >> (i & 31)) & 1u);
+      rounds[s0 + i] = hn[Bp + i];
+      if (status) status[s0 + i] = hn[2 * Bp + i];
+      any_cap |= hn[2 * Bp + i] != 0;
+    }
+  }
+  return any_cap ? DP_CAP_HIT : DP_OK;
+}
+
+}  // namespace
+
+extern "C" int dp_propagate_nodes(dp_ctx *ctx, const dp_matrix *mat, int32_t count,
+                                  const double *lb, const double *ub, const uint8_t *vartype,
+                                  const double *lhs, const double *rhs,
+                                  const dp_params *params, double *lb_out, double *ub_out,
+                                  int32_t *infeasible, int32_t *rounds, int32_t *status) {
+  return nodes_call(ctx, mat, count, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
+                    infeasible, rounds, status, false, nullptr, nullptr);
+}
+
+extern "C" int dp_propagate_nodes_hostloop(dp_ctx *ctx, const dp_matrix *mat, int32_t count,
+                                           const double *lb, const double *ub,
+                                           const uint8_t *vartype, const double *lhs,
+                                           const double *rhs, const dp_params *params,
+                                           double *lb_out, double *ub_out,
+                                           int32_t *infeasible, int32_t *rounds,
+                                           int32_t *status, float *kernel_ms,
+                                           int32_t *kernel_launches) {
+  if (kernel_ms)
+    for (int k = 0; k < kBatchStages; ++k) kernel_ms[k] = 0.0f;
+  if (kernel_launches)
+    for (int k = 0; k < kBatchStages; ++k) kernel_launches[k] = 0;
+  return nodes_call(ctx, mat, count, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
+                    infeasible, rounds, status, true, kernel_ms, kernel_launches);
+}

@@ -1,0 +1,273 @@
+// Device helpers shared by the single-instance round kernels (dp_kernels.cu)
+// and the batched-node kernels (dp_batch.cu): IEEE bit tests, the
+// order-preserving binary64 <-> int64 key map used by the bound atomics,
+// directed binary32 conversions, the binary32 screen, and the per-row
+// decisions of Step 2 (arXiv 2009.07785, Sec. 1.1).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cfloat>
+
+#include "dp_internal.h"
+
+namespace dp {
+
+// ---------------------------------------------------------------- helpers --
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ float f_inf() { return __uint_as_float(0x7F800000u); }
+
+__device__ __forceinline__ bool d_isinf(double x) {
+  return ((unsigned long long)__double_as_longlong(x) << 1) == 0xFFE0000000000000ull;
+}
+__device__ __forceinline__ bool d_isfinite(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7FF) != 0x7FF;
+}
+__device__ __forceinline__ bool d_isnan(double x) {
+  return ((unsigned long long)__double_as_longlong(x) << 1) > 0xFFE0000000000000ull;
+}
+__device__ __forceinline__ bool d_is_neginf(double x) {
+  return (unsigned long long)__double_as_longlong(x) == 0xFFF0000000000000ull;
+}
+__device__ __forceinline__ bool d_is_posinf(double x) {
+  return (unsigned long long)__double_as_longlong(x) == 0x7FF0000000000000ull;
+}
+__device__ __forceinline__ double d_abs(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+}
+// coefficient sign without an FP64 comparison (coefficients are nonzero)
+__device__ __forceinline__ bool d_pos(double a) { return __double2hiint(a) >= 0; }
+
+// Order-preserving map between binary64 values and signed 64-bit keys, so
+// that integer atomicMax/atomicMin implement max/min of doubles.
+__device__ __forceinline__ long long key_of(double x) {
+  long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double val_of_key(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFll));
+}
+
+// Exact floor / ceil of a binary64 value computed on the integer pipe from
+// the IEEE 754 binary64 layout (1 sign, 11 exponent, 52 fraction bits):
+// clear the fraction bits below the binary point; a negative value with a
+// nonzero cleared part moves one unit away from zero (a carry out of the
+// fraction field correctly bumps the exponent).  Keeps binary64 pipe time for
+// the arithmetic that needs it.
+__device__ __forceinline__ double d_floor_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFull) - 1023;
+  const bool neg = (b >> 63) != 0ull;
+  if (e >= 52) return x;  // integral, infinite or NaN
+  if (e < 0) {            // |x| < 1
+    if (!neg) return 0.0;
+    return ((b << 1) == 0ull) ? x : -1.0;  // -0 stays -0
+  }
+  const unsigned long long unit = 1ull << (52 - e);
+  const unsigned long long frac = unit - 1ull;
+  if ((b & frac) == 0ull) return x;
+  unsigned long long t = b & ~frac;
+  if (neg) t += unit;
+  return __longlong_as_double((long long)t);
+}
+__device__ __forceinline__ double d_ceil_int(double x) {
+  return -d_floor_int(-x);
+}
+// x > y for non-NaN binary64 values, on the integer pipe: order-preserving
+// keys with -0 folded onto +0 (IEEE comparison treats them as equal).
+__device__ __forceinline__ long long cmp_key(double x) {
+  long long b = __double_as_longlong(x);
+  if (((unsigned long long)b << 1) == 0ull) b = 0;
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+// |x| < t for a positive (possibly infinite) t; false for NaN x.
+__device__ __forceinline__ bool d_abs_lt(double x, double t) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) <
+         (unsigned long long)__double_as_longlong(t);
+}
+// max(1, |x|) for non-NaN x, by selection.
+__device__ __forceinline__ double d_max1abs(double x) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  return a >= 0x3FF0000000000000ull ? __longlong_as_double((long long)a) : 1.0;
+}
+
+// A binary32 value >= x, from the bit pattern (IEEE 754 field layout), with
+// no FP64-pipe conversion.  Truncates the significand toward zero and steps
+// one unit up when bits were dropped from a positive value.
+__device__ __forceinline__ float f32_up(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  unsigned mh = hi & 0x7FFFFFFFu;
+  bool neg = (hi >> 31) != 0;
+  unsigned e = mh >> 20;
+  if (e == 0x7FFu) return __uint_as_float((hi & 0x80000000u) | 0x7F800000u);
+  if (e >= 1151u) return neg ? -FLT_MAX : f_inf();
+  if (e < 897u) {
+    if (neg) return -0.0f;
+    return (mh | lo) ? FLT_MIN : 0.0f;
+  }
+  unsigned t = ((mh << 3) | (lo >> 29)) - (896u << 23);
+  bool exact = (lo & 0x1FFFFFFFu) == 0u;
+  if (!neg) return __uint_as_float(exact ? t : t + 1u);
+  return -__uint_as_float(t);
+}
+__device__ __forceinline__ float f32_dn(double x) { return -f32_up(-x); }
+
+// Upper bound on |a| as binary32, exact when |a| is a binary32 value, for
+// |a| in [2^-126, 2^127); rows holding a coefficient outside [2^-120, 2^120]
+// are flagged on the host and never use this value.
+__device__ __forceinline__ float absup_fast(double a) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  unsigned mh = (unsigned)(b >> 32) & 0x7FFFFFFFu, lo = (unsigned)b;
+  unsigned t = ((mh << 3) | (lo >> 29)) - (896u << 23);
+  return __uint_as_float(t + ((lo & 0x1FFFFFFFu) != 0u));
+}
+
+// ---- the binary32 screen ---------------------------------------------------
+//
+// For a > 0 the upper-bound candidate of x_j from the right-hand side is, in
+// exact arithmetic, L_j + s/a with s = rhs - minact; it is applied only if
+// it lies below U_j - tau*max(1,|U_j|) (continuous) or, after rounding,
+// below U_j (integer: L_j + s/a < U_j - eps_int).  So it can only be applied
+// if  s < |a| WU_j  with  WU_j = U_j - L_j - tau*max(1,|U_j|)  (continuous)
+// or  U_j - L_j - eps_int  (integer).  The three other sign/side cases give
+// the same form with WL_j (lower candidates use max(1,|L_j|)):
+//   right-hand side: a > 0 -> upper (WU), a < 0 -> lower (WL)
+//   left-hand side:  a > 0 -> lower (WL), a < 0 -> upper (WU)
+// The record stores binary32 upper bounds of WU, WL enlarged by
+// 2^-40 (|L|+|U|), clamped at 0; a row side stores a binary32 lower bound
+// thr of s - 2^-39 (|side| + |activity|).  These margins exceed the rounding
+// of every binary64 operation of the candidate formula and of the
+// acceptance threshold, so  upper(|a|) * W <= thr  proves that the
+// nonzero's candidate from that side is not applied.
+
+__device__ __forceinline__ void screen_widths(double L, double U, bool isint, float tau_dn,
+                                              float eps_dn, float &WU, float &WL) {
+  float base = __fsub_ru(f32_up(U), f32_dn(L));
+  if (!(base <= FLT_MAX)) {  // an infinite (or unrepresentable) width
+    WU = WL = f_inf();
+    return;
+  }
+  float absorb = __fmul_ru(0x1p-40f, __fadd_ru(f32_up(d_abs(L)), f32_up(d_abs(U))));
+  float cu, cl;
+  if (isint) {
+    cu = cl = eps_dn;
+  } else {
+    cu = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn(d_abs(U))));
+    cl = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn(d_abs(L))));
+  }
+  WU = fmaxf(__fadd_ru(__fsub_ru(base, cu), absorb), 0.0f);
+  WL = fmaxf(__fadd_ru(__fsub_ru(base, cl), absorb), 0.0f);
+  if (!(WU == WU)) WU = f_inf();  // never NaN (inf - inf on invalid input)
+  if (!(WL == WL)) WL = f_inf();
+}
+
+__device__ __forceinline__ void ld_rec(const VarRec *p, double &L, double &U, float &WU,
+                                       float &WL, uint32_t &flags) {
+  double d2, d3;
+  asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+      : "=d"(L), "=d"(U), "=d"(d2), "=d"(d3)
+      : "l"(p));
+  long long w = __double_as_longlong(d2);
+  WU = __int_as_float((int)(w & 0xFFFFFFFFll));
+  WL = __int_as_float((int)((unsigned long long)w >> 32));
+  flags = (uint32_t)((unsigned long long)__double_as_longlong(d3) & 0xFFFFFFFFull);
+}
+
+__device__ __forceinline__ void st_rec(VarRec *p, double L, double U, float WU, float WL,
+                                       uint32_t flags) {
+  long long w = (long long)(((unsigned long long)__float_as_uint(WL) << 32) |
+                            (unsigned long long)__float_as_uint(WU));
+  double d2 = __longlong_as_double(w);
+  double d3 = __longlong_as_double((long long)flags);
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(L), "d"(U), "d"(d2),
+               "d"(d3)
+               : "memory");
+}
+
+__device__ __forceinline__ void write_var(VarRec *p, double L, double U, uint32_t vt,
+                                          float tau_dn, float eps_dn) {
+  float WU, WL;
+  screen_widths(L, U, vt != 0u, tau_dn, eps_dn, WU, WL);
+  st_rec(p, L, U, WU, WL, vt);
+}
+
+__device__ __forceinline__ void set_flag(int32_t *f) {
+  atomicExch(f, 1);
+  __threadfence();
+}
+
+// ------------------------------------------------------- per-row decisions --
+
+// What the candidate step needs to know about one row (kept in shared
+// memory so that any lane of the warp can process any lane's nonzeros).
+struct RowView {
+  double minfin, maxfin, lhs, rhs;
+  int32_t mininf, maxinf;
+  float thr_r, thr_l;
+  int32_t exact;
+  int32_t act;  // some nonzero of the row may yield an accepted candidate
+};
+
+// Step 2 of Sec. 1.1 for both sides of a row, and the screen thresholds.
+__device__ __forceinline__ bool row_sides_eval(RowView &rv, float Tr, float Tl,
+                                               double eps_feas) {
+  bool infeas = false;
+  bool act_r = false, act_l = false;
+  rv.thr_r = f_inf();
+  rv.thr_l = f_inf();
+  if (d_isfinite(rv.rhs) && rv.mininf <= 1) {
+    if (rv.mininf == 1) {
+      act_r = true;  // only the nonzero with the infinite contribution
+    } else {
+      double s = rv.rhs - rv.minfin;
+      if (__double2hiint(s) < 0) {  // s < 0 (or -0, harmless)
+        double thr = rv.rhs + eps_feas * fmax(1.0, fabs(rv.rhs));
+        if (rv.minfin > thr) infeas = true;
+      }
+      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up(d_abs(rv.rhs)), f32_up(d_abs(rv.minfin))));
+      rv.thr_r = __fsub_rd(f32_dn(s), mg);
+      act_r = Tr > rv.thr_r;
+    }
+  }
+  if (d_isfinite(rv.lhs) && rv.maxinf <= 1) {
+    if (rv.maxinf == 1) {
+      act_l = true;
+    } else {
+      double s = rv.maxfin - rv.lhs;
+      if (__double2hiint(s) < 0) {
+        double thr = rv.lhs - eps_feas * fmax(1.0, fabs(rv.lhs));
+        if (rv.maxfin < thr) infeas = true;
+      }
+      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up(d_abs(rv.lhs)), f32_up(d_abs(rv.maxfin))));
+      rv.thr_l = __fsub_rd(f32_dn(s), mg);
+      act_l = Tl > rv.thr_l;
+    }
+  }
+  rv.act = (act_r || act_l) ? 1 : 0;
+  return infeas;
+}
+__device__ __forceinline__ void row_sides(RowView &rv, float Tr, float Tl, double eps_feas,
+                                          int32_t *infeasible_flag) {
+  if (row_sides_eval(rv, Tr, Tl, eps_feas)) set_flag(infeasible_flag);
+}
+
+// Which sides of one nonzero survive the screen (bit 0: right-hand side,
+// bit 1: left-hand side).
+__device__ __forceinline__ unsigned nnz_sides(double a, double L, double U, float WU,
+                                              float WL, const RowView &rv) {
+  bool pos = d_pos(a);
+  double bmin = pos ? L : U;
+  double bmax = pos ? U : L;
+  float au = absup_fast(a);
+  float tr = rv.exact ? f_inf() : __fmul_ru(au, pos ? WU : WL);
+  float tl = rv.exact ? f_inf() : __fmul_ru(au, pos ? WL : WU);
+  bool r = d_isfinite(rv.rhs) &&
+           ((rv.mininf == 0 && tr > rv.thr_r) || (rv.mininf == 1 && d_isinf(bmin)));
+  bool l = d_isfinite(rv.lhs) &&
+           ((rv.maxinf == 0 && tl > rv.thr_l) || (rv.maxinf == 1 && d_isinf(bmax)));
+  return (r ? 1u : 0u) | (l ? 2u : 0u);
+}
+
+}  // namespace dp

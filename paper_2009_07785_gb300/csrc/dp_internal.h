@@ -118,4 +118,64 @@ struct DevState {
   Ctrl *ctrl;
 };
 
+// ------------------------------------------------------ batched B&B nodes --
+//
+// One batched call propagates Bp = 32*G bound vectors ("nodes") over one
+// matrix.  Bounds are stored node-minor, entry e = j*Bp + node, so that the
+// 32 lanes of a warp (32 nodes of one node group g) read the bounds of one
+// variable with one 512-byte coalesced load, while the matrix row is read
+// once per warp with warp-uniform loads.
+constexpr int kMaxGroups = 32;              // at most 1024 nodes per launch
+
+// Partial activity of one chunk of a split row for one node.
+struct alignas(16) BPartial {
+  double minfin, maxfin;
+  int32_t mininf, maxinf;
+  float tr, tl;   // largest screen values of the chunk (right / left side)
+};
+
+// Combined activity of one split row for one node, with its screen
+// thresholds (a nonzero with |a| W <= thr cannot tighten from that side).
+struct alignas(16) BRowTot {
+  double minfin, maxfin;
+  int32_t mininf, maxinf;
+  float thr_r, thr_l;
+};
+
+struct BCtrl {
+  int32_t round;      // executed rounds
+  int32_t max_rounds;
+  int32_t B;          // real nodes
+  int32_t Bp;         // padded nodes (32*G)
+  int32_t G;          // node groups
+  int32_t err;        // 0, or a DP_ERR_* code found by the prologue
+  int32_t any_alive;  // some node is still propagating
+  uint32_t blocks_done;
+  int32_t ndirty[2];  // entries of the two dirty lists
+  int32_t icount[kMaxGroups];  // work items of each node group this round
+  double eps_int, tau_rel, eps_feas, inf_thr;
+};
+
+struct BatchState {
+  double2 *cur;         // [n*Bp] {L, U} at the start of the round
+  long long *nkey;      // [2*n*Bp] next state as order-preserving keys
+  uint32_t *chg[2];     // [n*G] nodes of each group whose bounds of var j changed
+  uint32_t *dirty[2];   // [2*n*Bp] entries e = j*Bp+node improved in a round
+  uint32_t *cmask;      // [nslots*G] nodes of each group that process a chunk
+  int32_t *items;       // [G*nslots] chunk slots to process, one region per group
+  BPartial *part;       // [nsplit_slots*Bp]
+  BRowTot *rowtot;      // [nsplit_rows*Bp]
+  uint32_t *srow_act;   // [nsplit_rows*G] nodes whose split row yields candidates
+  uint32_t *inf_bits;   // [kMaxGroups] nodes whose infeasibility was detected
+  uint32_t *chg_bits;   // [kMaxGroups] nodes with a changed bound this round
+  int32_t *node_rounds; // [Bp] rounds executed for the node
+  int32_t *node_status; // [Bp] 1 = stopped by the round cap
+  int32_t *node_done;   // [Bp]
+  uint32_t *alive;      // [G] nodes still propagating
+  double *lhs, *rhs;    // [m] normalised sides
+  uint8_t *vt;          // [n] 0/1 variable types
+  BCtrl *ctrl;
+  int64_t nslots;       // chunk slots (the capacity of one item region)
+};
+
 }  // namespace dp

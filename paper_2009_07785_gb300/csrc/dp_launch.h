@@ -29,6 +29,23 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S,
                                  int use_cond, int num_sms, cudaStream_t st,
                                  cudaEvent_t *ev);
 
+// Batched branch-and-bound nodes (dp_batch.cu).  The prologue normalises
+// `count` node-major bound vectors (lb[node*n + j]) into the node-minor
+// state; the epilogue writes them back node-major.
+cudaError_t launch_batch_prologue(const DevMatrix &M, const BatchState &S, int32_t count,
+                                  const double *lb, const double *ub, const uint8_t *vartype,
+                                  const double *lhs, const double *rhs, double eps_int,
+                                  double eps_feas, double thr, int num_sms, cudaStream_t st);
+cudaError_t launch_batch_epilogue(const DevMatrix &M, const BatchState &S, int32_t count,
+                                  double *lb_out, double *ub_out, int num_sms,
+                                  cudaStream_t st);
+// One batched round; in a graph body (use_cond = 1) the last kernel sets
+// the WHILE condition.  With `ev` (12 events) each of the six stages (mark,
+// mark_split, act, combine, cand_split, finish) is bracketed by a pair.
+cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
+                               cudaGraphConditionalHandle handle, int use_cond,
+                               int num_sms, cudaStream_t st, cudaEvent_t *ev);
+
 // Host image of the device layout described in dp_internal.h.
 struct HostLayout {
   int32_t m = 0, n = 0;

@@ -139,6 +139,8 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
       out.slice_len[s] = L;
       total += (int64_t)L * kSliceW;
     }
+    // candidate work lists address elements with 32-bit offsets
+    if (total >= (int64_t(1) << 32)) return DP_ERR_INVALID_ARG;
     out.val.assign((size_t)total, 0.0);
     out.col.assign((size_t)total, 0);
     out.chunk_row.resize(nslots);
