@@ -33,9 +33,6 @@ __device__ __forceinline__ bool d_is_neginf(double x) {
 __device__ __forceinline__ bool d_is_posinf(double x) {
   return (unsigned long long)__double_as_longlong(x) == 0x7FF0000000000000ull;
 }
-__device__ __forceinline__ double d_abs(double x) {
-  return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
-}
 // coefficient sign without an FP64 comparison (coefficients are nonzero)
 __device__ __forceinline__ bool d_pos(double a) { return __double2hiint(a) >= 0; }
 
@@ -92,11 +89,12 @@ __device__ __forceinline__ double d_max1abs(double x) {
   return a >= 0x3FF0000000000000ull ? __longlong_as_double((long long)a) : 1.0;
 }
 
-// A binary32 value >= x, from the bit pattern (IEEE 754 field layout), with
-// no FP64-pipe conversion.  Truncates the significand toward zero and steps
-// one unit up when bits were dropped from a positive value.
-__device__ __forceinline__ float f32_up(double x) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+// A binary32 value >= x, from the bit pattern b of x (IEEE 754 field
+// layout), with no binary64-pipe work.  Truncates the significand toward
+// zero and steps one unit up when bits were dropped from a positive value.
+// Sign changes and absolute values are applied to the bit pattern (never to
+// a binary64 value, which would cost a binary64-pipe instruction).
+__device__ __forceinline__ float f32_up_bits(unsigned long long b) {
   unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   unsigned mh = hi & 0x7FFFFFFFu;
   bool neg = (hi >> 31) != 0;
@@ -112,7 +110,16 @@ __device__ __forceinline__ float f32_up(double x) {
   if (!neg) return __uint_as_float(exact ? t : t + 1u);
   return -__uint_as_float(t);
 }
-__device__ __forceinline__ float f32_dn(double x) { return -f32_up(-x); }
+constexpr unsigned long long kSign64 = 0x8000000000000000ull;
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ float f32_up(double x) { return f32_up_bits(dbits(x)); }
+// a binary32 value <= x
+__device__ __forceinline__ float f32_dn(double x) { return -f32_up_bits(dbits(x) ^ kSign64); }
+// binary32 bounds of |x| from above and below
+__device__ __forceinline__ float f32_up_abs(double x) { return f32_up_bits(dbits(x) & ~kSign64); }
+__device__ __forceinline__ float f32_dn_abs(double x) { return -f32_up_bits(dbits(x) | kSign64); }
 
 // Upper bound on |a| as binary32, exact when |a| is a binary32 value, for
 // |a| in [2^-126, 2^127); rows holding a coefficient outside [2^-120, 2^120]
@@ -149,13 +156,13 @@ __device__ __forceinline__ void screen_widths(double L, double U, bool isint, fl
     WU = WL = f_inf();
     return;
   }
-  float absorb = __fmul_ru(0x1p-40f, __fadd_ru(f32_up(d_abs(L)), f32_up(d_abs(U))));
+  float absorb = __fmul_ru(0x1p-40f, __fadd_ru(f32_up_abs(L), f32_up_abs(U)));
   float cu, cl;
   if (isint) {
     cu = cl = eps_dn;
   } else {
-    cu = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn(d_abs(U))));
-    cl = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn(d_abs(L))));
+    cu = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn_abs(U)));
+    cl = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn_abs(L)));
   }
   WU = fmaxf(__fadd_ru(__fsub_ru(base, cu), absorb), 0.0f);
   WL = fmaxf(__fadd_ru(__fsub_ru(base, cl), absorb), 0.0f);
@@ -226,7 +233,7 @@ __device__ __forceinline__ bool row_sides_eval(RowView &rv, float Tr, float Tl,
         double thr = rv.rhs + eps_feas * fmax(1.0, fabs(rv.rhs));
         if (rv.minfin > thr) infeas = true;
       }
-      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up(d_abs(rv.rhs)), f32_up(d_abs(rv.minfin))));
+      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up_abs(rv.rhs), f32_up_abs(rv.minfin)));
       rv.thr_r = __fsub_rd(f32_dn(s), mg);
       act_r = Tr > rv.thr_r;
     }
@@ -240,7 +247,7 @@ __device__ __forceinline__ bool row_sides_eval(RowView &rv, float Tr, float Tl,
         double thr = rv.lhs - eps_feas * fmax(1.0, fabs(rv.lhs));
         if (rv.maxfin < thr) infeas = true;
       }
-      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up(d_abs(rv.lhs)), f32_up(d_abs(rv.maxfin))));
+      float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up_abs(rv.lhs), f32_up_abs(rv.maxfin)));
       rv.thr_l = __fsub_rd(f32_dn(s), mg);
       act_l = Tl > rv.thr_l;
     }
