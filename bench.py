@@ -15,6 +15,9 @@ roofline: the activity/candidate kernel (k_round), algorithmic bytes
           with the host-driven loop variant right after the timed region.
 cpu_baseline / --impl reference: the CPU oracle (one thread) on a bounded
           number of rounds of the same workload.
+batched_nodes: 256 branch-and-bound node bound vectors over the medium
+          matrix (m=200k, ~2M nonzeros) propagated by one dp_propagate_nodes
+          call, against the plain loop of one dp_propagate call per node.
 
 Multi-GPU (torchrun): replicas -- every rank propagates its own copy of the
 workload; there is no data-path collective (scaling: weak).
@@ -54,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-nodes", action="store_true",
+                    help="skip the batched branch-and-bound node measurement")
     return ap.parse_args()
 
 
@@ -228,6 +233,69 @@ def run_reference(args):
     return 0
 
 
+def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3):
+    """Batched branch-and-bound nodes (dp_propagate_nodes, one call for all
+    nodes) against the plain loop (one dp_propagate call per node, the same
+    kernels' single-instance path) on the medium matrix, device-resident
+    inputs, CUDA events on the library's stream.  Two node sets: fixings at
+    random in-domain values (the stated workload; most nodes are infeasible
+    after round 1) and fixings at the feasible point's values (every node
+    runs to its fixed point)."""
+    import torch
+    from paper_2009_07785_gb300 import synth
+
+    inst = synth.medium()
+    mat = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    vt, lhs, rhs = dev(inst.vartype), dev(inst.lhs), dev(inst.rhs)
+    seed = synth.seed_for(3, 0)
+    sets = {"random_values": synth.node_bounds(inst, count, seed=seed),
+            "feasible_point_values": synth.node_bounds_at_point(inst, count, seed=seed)}
+    out = {"workload": f"{inst.name}: m={inst.m} n={inst.n} nnz={inst.nnz}, {count} node bound "
+                       f"vectors fixing 1-5% of the integer variables (seed {seed})",
+           "count": count}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for name, (LB, UB) in sets.items():
+        dLB, dUB = dev(LB), dev(UB)
+        lo, hi = torch.empty_like(dLB), torch.empty_like(dUB)
+        for _ in range(warmup):
+            r = dp.dp_propagate_nodes(ctx, mat, dLB, dUB, vt, lhs, rhs, lb_out=lo, ub_out=hi)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            r = dp.dp_propagate_nodes(ctx, mat, dLB, dUB, vt, lhs, rhs, lb_out=lo, ub_out=hi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) / reps
+        rows = [(dLB[k].contiguous(), dUB[k].contiguous()) for k in range(count)]
+        o1 = torch.empty(inst.n, dtype=torch.float64, device="cuda")
+        o2 = torch.empty_like(o1)
+        for k in range(warmup):
+            dp.dp_propagate(ctx, mat, rows[k][0], rows[k][1], vt, lhs, rhs, lb_out=o1, ub_out=o2)
+        torch.cuda.synchronize()
+        rounds_plain = []
+        e0.record(stream)
+        for k in range(count):
+            rp = dp.dp_propagate(ctx, mat, rows[k][0], rows[k][1], vt, lhs, rhs, lb_out=o1,
+                                 ub_out=o2)
+            rounds_plain.append(rp.rounds)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_plain = e0.elapsed_time(e1)
+        assert np.array_equal(np.asarray(rounds_plain), r.rounds), "batched and plain rounds differ"
+        h = dp.dp_propagate_nodes_hostloop(ctx, mat, dLB, dUB, vt, lhs, rhs, lb_out=lo, ub_out=hi)
+        out[name] = {"nodes_per_s": count / (t_batch * 1e-3),
+                     "plain_loop_nodes_per_s": count / (t_plain * 1e-3),
+                     "speedup_vs_plain_loop": t_plain / t_batch,
+                     "ms_per_batch": round(t_batch, 3), "plain_loop_ms": round(t_plain, 3),
+                     "rounds_mean": float(r.rounds.mean()), "rounds_max": int(r.rounds.max()),
+                     "infeasible_nodes": int(r.infeasible.sum()),
+                     "stage_ms": {k: round(v, 3) for k, v in zip(dp.NODE_STAGES, h.kernel_ms)}}
+    mat.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -333,6 +401,10 @@ def run_ours(args):
                "sample": f"first {r_cpu} of {rounds} rounds of the same workload from its initial "
                          f"bounds, single-threaded C oracle ({el:.1f} s)"}
 
+    nodes = None
+    if ws == 1 and not args.no_nodes:
+        nodes = nodes_bench(dp, ctx, stream)
+
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -347,7 +419,7 @@ def run_ours(args):
                           "l2": "no flush: the matrix streamed each round (0.36 GB) exceeds the 129 MB L2",
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk}
+               "clocks": clk, "batched_nodes": nodes}
         print(json.dumps(out))
     mat.close()
     ctx.close()

@@ -279,6 +279,23 @@ def node_bounds(inst: Instance, count: int, seed: int, lo_frac=0.01, hi_frac=0.0
     return LB, UB
 
 
+def node_bounds_at_point(inst: Instance, count: int, seed: int, lo_frac=0.01, hi_frac=0.05):
+    """Node bound vectors that fix a random 1-5% of the integer variables to
+    their value in the instance's feasible point x* (every node stays
+    feasible, as nodes on the path to a solution do).  Returns
+    (lb[count, n], ub[count, n])."""
+    rng = np.random.default_rng(seed)
+    ints = np.flatnonzero((inst.vartype == 1) & np.isfinite(inst.lb) & np.isfinite(inst.ub))
+    LB = np.repeat(inst.lb[None, :], count, axis=0)
+    UB = np.repeat(inst.ub[None, :], count, axis=0)
+    for b in range(count):
+        k = max(1, int(round(rng.uniform(lo_frac, hi_frac) * ints.size)))
+        pick = rng.choice(ints, size=min(k, ints.size), replace=False)
+        LB[b, pick] = inst.xstar[pick]
+        UB[b, pick] = inst.xstar[pick]
+    return LB, UB
+
+
 def small_random(rng: np.random.Generator, m: int, n: int, maxlen: int, int_frac=0.6,
                  coef=(1, 10), inf_frac=0.1, ranged_frac=0.2, slack_mean=2.0,
                  pure_integer=False, bounded=False) -> Instance:
