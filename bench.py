@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-nodes", action="store_true",
                     help="skip the batched branch-and-bound node measurement")
+    ap.add_argument("--nodes-only", action="store_true",
+                    help="run only the batched node measurement (profiling captures)")
+    ap.add_argument("--nodes-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -92,14 +95,20 @@ def peaks():
     return PEAK_FALLBACK_GBS, "fallback"
 
 
+def kernel_source_sha():
+    """Hash of the sources that define k_round (kernel file + device helpers)."""
+    csrc = ROOT / "paper_2009_07785_gb300" / "csrc"
+    data = b"".join((csrc / f).read_bytes() for f in ("dp_kernels.cu", "dp_device.cuh"))
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
 def ncu_traffic():
     """Per-launch DRAM bytes of k_round from the committed ncu summary, or
     None if the kernel source changed since that capture."""
     f = ROOT / "profiles" / "ncu_k_round_large.md"
-    src = ROOT / "paper_2009_07785_gb300" / "csrc" / "dp_kernels.cu"
     if not f.exists():
         return None
-    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    h = kernel_source_sha()
     text = f.read_text()
     kv = {}
     for line in text.splitlines():
@@ -310,6 +319,12 @@ def run_ours(args):
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = tdist
     _build.build()
+    if args.nodes_only:
+        ctx = dp.Context(local, torch.cuda.current_stream())
+        print(json.dumps({"batched_nodes": nodes_bench(dp, ctx, torch.cuda.current_stream(),
+                                                       count=args.nodes_count)}))
+        ctx.close()
+        return 0
     inst = make_workload(args.workload, args.scale)
     stream = torch.cuda.current_stream()
     ctx = dp.Context(local, stream)
@@ -403,7 +418,7 @@ def run_ours(args):
 
     nodes = None
     if ws == 1 and not args.no_nodes:
-        nodes = nodes_bench(dp, ctx, stream)
+        nodes = nodes_bench(dp, ctx, stream, count=args.nodes_count)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
