@@ -779,6 +779,7 @@ k_bprologue_bounds(BatchState S, int32_t n, int32_t count, int32_t Bp, const dou
                    double thr) {
   __shared__ double sL[32][33], sU[32][33];
   const double pinf = __longlong_as_double(0x7FF0000000000000ll);
+  const long long k_thr = cmp_key(thr), k_mthr = cmp_key(-thr);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int G = Bp / 32;
   const int64_t tiles_x = ((int64_t)n + 31) / 32;
@@ -794,22 +795,24 @@ k_bprologue_bounds(BatchState S, int32_t n, int32_t count, int32_t Bp, const dou
       if (node < count && j < n) {
         L = lb[(int64_t)node * n + j];
         U = ub[(int64_t)node * n + j];
-        if (d_isnan(L) || d_isnan(U) || L >= thr || U <= -thr) {
+        // comparisons with +-thr on order-preserving keys (integer pipe;
+        // the same decisions as the binary64 comparisons for non-NaN values)
+        if (d_isnan(L) || d_isnan(U) || cmp_key(L) >= k_thr || cmp_key(U) <= k_mthr) {
           bad = true;
           L = 0.0;
           U = 0.0;
         }
-        if (L <= -thr) L = -pinf;
-        if (U >= thr) U = pinf;
+        if (cmp_key(L) <= k_mthr) L = -pinf;
+        if (cmp_key(U) >= k_thr) U = pinf;
         const bool isint = vartype[j] != 0;
         if (isint) {
-          if (d_isfinite(L)) L = ceil(L - eps_int);
-          if (d_isfinite(U)) U = floor(U + eps_int);
+          if (d_isfinite(L)) L = d_ceil_int(L - eps_int);
+          if (d_isfinite(U)) U = d_floor_int(U + eps_int);
         }
         // Bounds that already cross: the crossing test of round 1 covers
         // every variable, and tightening cannot undo a crossing, so the
         // node is flagged now and ends after its first round.
-        if (L > U && (isint || L > U + eps_feas * fmax(1.0, fabs(U))))
+        if (cmp_key(L) > cmp_key(U) && (isint || L > U + eps_feas * fmax(1.0, fabs(U))))
           atomicOr(&S.inf_bits[node >> 5], 1u << (node & 31));
       }
       sL[yy][tx] = L;
