@@ -271,6 +271,97 @@ int dp_propagate_nodes_hostloop(dp_ctx *ctx, const dp_matrix *mat,
                                 int32_t *rounds, int32_t *status,
                                 float *kernel_ms, int32_t *kernel_launches);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  The paper has no
+ * counterpart (it propagates one problem per call); this is how a solver
+ * service keeps a GPU busy with many small propagations (Sec. 5: nodes a
+ * few bound changes away from a propagated state).
+ *
+ * A server keeps matrices resident (dp_server_add_matrix) and answers
+ * requests (dp_server_submit): one node bound vector of a resident matrix,
+ * propagated exactly as dp_propagate would propagate it alone.  Each
+ * resident matrix runs a batch of `slots` node slots on its own stream,
+ * round by round; between two rounds, finished nodes are read out and
+ * their slots are given to waiting requests, which join the running batch
+ * (continuous batching).  A matrix's device workspace is allocated when it
+ * first has work, within `mem_budget` bytes for all matrices (admission by
+ * device memory; idle matrices give theirs back when another needs room).
+ * Requests beyond the free slots and memory wait in arrival order.
+ * All functions are thread-safe; a worker thread owned by the server does
+ * all device work.
+ * ---------------------------------------------------------------------- */
+typedef struct dp_server dp_server;
+
+typedef struct {
+  int32_t slots;        /* node slots per resident matrix: a multiple of 32,
+                           32..1024 (0 = 64) */
+  int32_t reserved0;
+  int64_t mem_budget;   /* device bytes for all matrices' workspaces
+                           (<= 0: half of the free device memory at
+                           creation) */
+  dp_params params;     /* shared by every request (max_rounds >= 1) */
+} dp_server_config;
+
+typedef struct {
+  uint64_t tag;         /* the tag given to dp_server_submit */
+  int32_t status;       /* DP_OK or DP_CAP_HIT */
+  int32_t infeasible;   /* as in dp_propagate */
+  int32_t rounds;       /* as in dp_propagate */
+  int32_t matrix;       /* matrix id */
+  double arrival_us;    /* arrival time (dp_server_clock_us scale) */
+  double done_us;       /* time the result was written to lb_out/ub_out */
+} dp_completion;
+
+typedef struct {
+  int64_t submitted, completed, in_system;
+  int64_t rounds;            /* batched rounds launched (all matrices) */
+  int64_t slot_rounds;       /* sum over rounds of the propagating nodes */
+  int64_t admissions;        /* requests placed into slots */
+  int64_t max_active_slots;  /* largest number of propagating nodes of a round */
+  int64_t workspaces_allocated, evictions;
+  int64_t device_bytes;      /* workspace bytes currently held */
+} dp_server_stats;
+
+/* Creates a server on ctx's device (cfg NULL: 64 slots, half of the free
+ * memory, dp_params_default()).  Returns DP_OK, DP_ERR_INVALID_ARG,
+ * DP_ERR_OOM or DP_ERR_CUDA. */
+int dp_server_create(dp_ctx *ctx, const dp_server_config *cfg,
+                     dp_server **out);
+
+/* Makes a loaded matrix (of the server's context) resident with its
+ * variable types and sides (host or device; copied).  The matrix must
+ * outlive the server.  *matrix_id receives its id (0, 1, ...). */
+int dp_server_add_matrix(dp_server *s, const dp_matrix *mat,
+                         const uint8_t *vartype, const double *lhs,
+                         const double *rhs, int32_t *matrix_id);
+
+/* Queues one request: lb[n], ub[n] (HOST memory, read when the request is
+ * admitted) and lb_out[n], ub_out[n] (HOST memory, written when it
+ * completes) must stay valid until its completion is polled.  arrival_us is
+ * the request's arrival time on the dp_server_clock_us scale (<= 0: now);
+ * latency is measured from it.  The bounds are checked here: NaN, lb >=
+ * inf_threshold or ub <= -inf_threshold return DP_ERR_NAN_INPUT and queue
+ * nothing. */
+int dp_server_submit(dp_server *s, int32_t matrix_id, const double *lb,
+                     const double *ub, double *lb_out, double *ub_out,
+                     uint64_t tag, double arrival_us);
+
+/* Moves up to max completions into out[] (*count of them), waiting up to
+ * wait_us microseconds for the first one when none is ready.  Returns
+ * DP_OK, or DP_ERR_CUDA once the worker has seen a device error. */
+int dp_server_poll(dp_server *s, dp_completion *out, int32_t max,
+                   int32_t *count, int32_t wait_us);
+
+/* Counters since creation. */
+int dp_server_stats_get(dp_server *s, dp_server_stats *out);
+
+/* Microseconds on the steady clock the server time-stamps with. */
+double dp_server_clock_us(void);
+
+/* Completes every submitted request, stops the worker and frees the
+ * server (not the matrices).  Returns DP_OK or the worker's error. */
+int dp_server_destroy(dp_server *s);
+
 #ifdef __cplusplus
 }
 #endif

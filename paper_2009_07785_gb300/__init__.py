@@ -32,12 +32,31 @@ DP_ERR_TIMEOUT = -6
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
            "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes",
-           "dp_propagate_nodes_hostloop")
+           "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
+           "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
+           "dp_server_destroy")
 
 
 class dp_params(C.Structure):
     _fields_ = [("max_rounds", C.c_int32), ("reserved0", C.c_int32), ("eps_int", C.c_double),
                 ("tau_rel", C.c_double), ("eps_feas", C.c_double), ("inf_threshold", C.c_double)]
+
+
+class dp_server_config(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("reserved0", C.c_int32), ("mem_budget", C.c_int64),
+                ("params", dp_params)]
+
+
+class dp_completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("infeasible", C.c_int32),
+                ("rounds", C.c_int32), ("matrix", C.c_int32), ("arrival_us", C.c_double),
+                ("done_us", C.c_double)]
+
+
+class dp_server_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in
+                ("submitted", "completed", "in_system", "rounds", "slot_rounds", "admissions",
+                 "max_active_slots", "workspaces_allocated", "evictions", "device_bytes")]
 
 
 _lib = None
@@ -86,6 +105,20 @@ def lib() -> C.CDLL:
                                               C.POINTER(dp_params), vp, vp, vp, vp, vp,
                                               C.POINTER(C.c_float), C.POINTER(i32)]
     L.dp_propagate_nodes_hostloop.restype = C.c_int
+    L.dp_server_create.argtypes = [vp, C.POINTER(dp_server_config), C.POINTER(vp)]
+    L.dp_server_create.restype = C.c_int
+    L.dp_server_add_matrix.argtypes = [vp, vp, vp, vp, vp, C.POINTER(i32)]
+    L.dp_server_add_matrix.restype = C.c_int
+    L.dp_server_submit.argtypes = [vp, i32, vp, vp, vp, vp, C.c_uint64, C.c_double]
+    L.dp_server_submit.restype = C.c_int
+    L.dp_server_poll.argtypes = [vp, C.POINTER(dp_completion), i32, C.POINTER(i32), i32]
+    L.dp_server_poll.restype = C.c_int
+    L.dp_server_stats_get.argtypes = [vp, C.POINTER(dp_server_stats)]
+    L.dp_server_stats_get.restype = C.c_int
+    L.dp_server_clock_us.argtypes = []
+    L.dp_server_clock_us.restype = C.c_double
+    L.dp_server_destroy.argtypes = [vp]
+    L.dp_server_destroy.restype = C.c_int
     _lib = L
     return L
 
@@ -343,3 +376,113 @@ def _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, hostloop
                            tuple(ms), tuple(cnt))
     rc = _check(lib().dp_propagate_nodes(*args), "dp_propagate_nodes")
     return NodesResult(lb_out, ub_out, inf[:count], rounds[:count], cap[:count], rc)
+
+
+# ------------------------------------------------------------------ serving --
+
+class Server:
+    """A dp_server: resident matrices and a request loop with continuous
+    batching (see include/domprop.h).  Requests are numpy float64 host
+    arrays; the binding keeps them alive until their completion is polled."""
+
+    def __init__(self, ctx: Context, slots: int = 64, mem_budget: int = 0,
+                 params: dp_params | None = None):
+        cfg = dp_server_config()
+        cfg.slots = int(slots)
+        cfg.mem_budget = int(mem_budget)
+        cfg.params = params if params is not None else dp_params_default()
+        h = C.c_void_p()
+        _check(lib().dp_server_create(ctx.handle, C.byref(cfg), C.byref(h)), "dp_server_create")
+        self.handle = h
+        self.ctx = ctx
+        self._n = {}
+        self._live = {}
+        self._next_tag = 1
+
+    def add_matrix(self, mat: Matrix, vartype, lhs, rhs) -> int:
+        mid = C.c_int32()
+        self._keep = getattr(self, "_keep", []) + [mat]
+        _check(lib().dp_server_add_matrix(self.handle, mat.handle, _ptr(vartype), _ptr(lhs),
+                                          _ptr(rhs), C.byref(mid)), "dp_server_add_matrix")
+        self._n[mid.value] = mat.n
+        return mid.value
+
+    def submit(self, matrix_id: int, lb, ub, lb_out=None, ub_out=None, tag: int | None = None,
+               arrival_us: float = 0.0) -> int:
+        n = self._n.get(matrix_id, 0)  # an unknown id is rejected by the library
+        lb = np.ascontiguousarray(lb, dtype=np.float64)
+        ub = np.ascontiguousarray(ub, dtype=np.float64)
+        if lb_out is None:
+            lb_out = np.empty(n)
+        if ub_out is None:
+            ub_out = np.empty(n)
+        if tag is None:
+            tag = self._next_tag
+            self._next_tag += 1
+        _check(lib().dp_server_submit(self.handle, int(matrix_id), _ptr(lb), _ptr(ub),
+                                      _ptr(lb_out), _ptr(ub_out), int(tag), float(arrival_us)),
+               "dp_server_submit")
+        self._live[int(tag)] = (lb, ub, lb_out, ub_out)
+        return int(tag)
+
+    def poll(self, max_count: int = 1024, wait_us: int = 0) -> list:
+        buf = (dp_completion * max_count)()
+        cnt = C.c_int32()
+        _check(lib().dp_server_poll(self.handle, buf, max_count, C.byref(cnt), int(wait_us)),
+               "dp_server_poll")
+        out = []
+        for i in range(cnt.value):
+            c = buf[i]
+            lb, ub, lo, hi = self._live.pop(int(c.tag))
+            out.append({"tag": int(c.tag), "status": c.status, "infeasible": c.infeasible,
+                        "rounds": c.rounds, "matrix": c.matrix, "arrival_us": c.arrival_us,
+                        "done_us": c.done_us, "lb": lo, "ub": hi})
+        return out
+
+    def stats(self) -> dict:
+        st = dp_server_stats()
+        _check(lib().dp_server_stats_get(self.handle, C.byref(st)), "dp_server_stats_get")
+        return {k: getattr(st, k) for k, _ in dp_server_stats._fields_}
+
+    def close(self) -> int:
+        rc = 0
+        if self.handle:
+            rc = lib().dp_server_destroy(self.handle)
+            self.handle = None
+        return rc
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def dp_server_create(ctx: Context, slots: int = 64, mem_budget: int = 0,
+                     params: dp_params | None = None) -> Server:
+    return Server(ctx, slots, mem_budget, params)
+
+
+def dp_server_add_matrix(server: Server, mat: Matrix, vartype, lhs, rhs) -> int:
+    return server.add_matrix(mat, vartype, lhs, rhs)
+
+
+def dp_server_submit(server: Server, matrix_id: int, lb, ub, lb_out=None, ub_out=None,
+                     tag: int | None = None, arrival_us: float = 0.0) -> int:
+    return server.submit(matrix_id, lb, ub, lb_out, ub_out, tag, arrival_us)
+
+
+def dp_server_poll(server: Server, max_count: int = 1024, wait_us: int = 0) -> list:
+    return server.poll(max_count, wait_us)
+
+
+def dp_server_stats_get(server: Server) -> dict:
+    return server.stats()
+
+
+def dp_server_clock_us() -> float:
+    return lib().dp_server_clock_us()
+
+
+def dp_server_destroy(server: Server) -> int:
+    return server.close()

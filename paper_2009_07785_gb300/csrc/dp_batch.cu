@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_bmark(DevMatrix M, BatchState S) {
   const BParams P = load_params(ctrl);
   if (P.err) return;
   const int p = P.round & 1;
-  const bool first = P.round == 0;
+  const bool first = P.round == 0;  // every live node is fresh
   const uint32_t *chg = S.chg[p];
   const int64_t nslots = S.nslots;
   const int64_t split_slots = (int64_t)M.nslices_split * kSliceW;
@@ -431,6 +431,8 @@ __global__ void __launch_bounds__(kThreads) k_bmark(DevMatrix M, BatchState S) {
           }
         }
         const uint4 al = *reinterpret_cast<const uint4 *>(S.alive + gq);
+        const uint4 fr = *reinterpret_cast<const uint4 *>(S.fresh + gq);
+        m = or4(m, fr);
         m = make_uint4(m.x & al.x, m.y & al.y, m.z & al.z, m.w & al.w);
         *reinterpret_cast<uint4 *>(S.cmask + cs * P.Gs + gq) = m;
       }
@@ -728,11 +730,13 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
   for (int node = threadIdx.x; node < P.Bp; node += blockDim.x) {
     int32_t d = S.node_done[node];
     if (!d && !P.err) {
+      // each node counts its own rounds (nodes admitted later start at 0)
       const uint32_t b = 1u << (node & 31);
-      S.node_rounds[node] = r;
+      const int32_t rn = S.node_rounds[node] + 1;
+      S.node_rounds[node] = rn;
       if (inf_bits[node >> 5] & b) d = 1;
       else if (!(chg_bits[node >> 5] & b)) d = 1;
-      else if (r >= P.max_rounds) {
+      else if (rn >= P.max_rounds) {
         d = 1;
         S.node_status[node] = 1;
       }
@@ -753,6 +757,7 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
   if (threadIdx.x < kMaxGroups) {
     ctrl->icount[threadIdx.x] = 0;
     S.chg_bits[threadIdx.x] = 0u;
+    S.fresh[threadIdx.x] = 0u;
   }
   if (threadIdx.x == 0) {
     volatile BCtrl *vc = ctrl;
@@ -841,6 +846,7 @@ __global__ void k_bprologue_misc(BatchState S, int32_t m, int32_t n, int32_t cou
   const int Gs = ((Bp / 32) + 3) & ~3;
   int64_t total = n > m ? n : m;
   if (total < Bp) total = Bp;
+  if (total < kMaxGroups) total = kMaxGroups;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (i < n) S.vt[i] = vartype[i] ? 1 : 0;
@@ -865,12 +871,13 @@ __global__ void k_bprologue_misc(BatchState S, int32_t m, int32_t n, int32_t cou
       S.node_status[i] = 0;
       S.node_done[i] = i < count ? 0 : 1;
     }
-    if (i < Gs) {
+    if (i < kMaxGroups) {
       const int64_t lo = i * 32;
       uint32_t w = 0u;
       for (int b = 0; b < 32; ++b)
-        if (lo + b < count) w |= 1u << b;
+        if (i < Gs && lo + b < count) w |= 1u << b;
       S.alive[i] = w;
+      S.fresh[i] = w;
     }
   }
 }
@@ -906,6 +913,103 @@ k_bepilogue(BatchState S, int32_t n, int32_t count, int32_t Bp, double *lb_out,
   }
 }
 
+// ------------------------------------------------- slots (request serving) --
+//
+// A long-running batch whose nodes are independent requests: between rounds
+// finished nodes are read out and their slots refilled with new requests,
+// which start with every row active (fresh) and count their own rounds.
+
+// Per-node state of newly admitted slots.  Thread per admitted slot.
+__global__ void k_bslot_reset(BatchState S, const int32_t *slots, int32_t count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int node = slots[i];
+  const uint32_t b = 1u << (node & 31);
+  S.node_done[node] = 0;
+  S.node_rounds[node] = 0;
+  S.node_status[node] = 0;
+  atomicAnd(&S.inf_bits[node >> 5], ~b);
+  atomicOr(&S.alive[node >> 5], b);
+  atomicOr(&S.fresh[node >> 5], b);
+}
+
+// Bounds of newly admitted slots: staged request vectors (slot i's lb at
+// stage + 2*i*n, its ub n entries later; already validated) normalised
+// into the slot's node column.  A crossing input flags the node.
+__global__ void __launch_bounds__(kThreads)
+k_bslot_fill(BatchState S, const int32_t *slots, int32_t count, const double *stage, int32_t n,
+             int32_t Bp, double eps_int, double eps_feas, double thr) {
+  const double pinf = __longlong_as_double(0x7FF0000000000000ll);
+  const long long k_thr = cmp_key(thr), k_mthr = cmp_key(-thr);
+  const int64_t total = (int64_t)count * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n, j = t % n;
+    const int node = slots[i];
+    double L = stage[2 * i * n + j], U = stage[(2 * i + 1) * n + j];
+    if (cmp_key(L) <= k_mthr) L = -pinf;
+    if (cmp_key(U) >= k_thr) U = pinf;
+    const bool isint = S.vt[j] != 0;
+    if (isint) {
+      if (d_isfinite(L)) L = d_ceil_int(L - eps_int);
+      if (d_isfinite(U)) U = d_floor_int(U + eps_int);
+    }
+    if (cmp_key(L) > cmp_key(U) && (isint || L > U + eps_feas * fmax(1.0, fabs(U))))
+      atomicOr(&S.inf_bits[node >> 5], 1u << (node & 31));
+    const int64_t e = j * Bp + node;
+    S.cur[e] = make_double2(L, U);
+    reinterpret_cast<longlong2 *>(S.nkey)[e] = make_longlong2(key_of(L), key_of(U));
+  }
+}
+
+// Bounds of finished slots into contiguous vectors (slot i's lb at
+// out + 2*i*n, its ub n entries later).
+__global__ void __launch_bounds__(kThreads)
+k_bslot_extract(BatchState S, const int32_t *slots, int32_t count, double *out, int32_t n,
+                int32_t Bp) {
+  const int64_t total = (int64_t)count * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n, j = t % n;
+    const double2 b = S.cur[j * Bp + slots[i]];
+    out[2 * i * n + j] = b.x;
+    out[(2 * i + 1) * n + j] = b.y;
+  }
+}
+
+// Sides, types and the empty per-node state of a serving batch (no node
+// occupied yet).
+__global__ void k_bslots_init(BatchState S, int32_t m, int32_t n, int32_t Bp,
+                              const uint8_t *vartype, const double *lhs, const double *rhs,
+                              double thr) {
+  const double pinf = __longlong_as_double(0x7FF0000000000000ll);
+  int64_t total = n > m ? n : m;
+  if (total < Bp) total = Bp;
+  if (total < kMaxGroups) total = kMaxGroups;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) S.vt[i] = vartype[i] ? 1 : 0;
+    if (i < m) {
+      double l = lhs[i], r = rhs[i];
+      if (l <= -thr) l = -pinf;
+      if (r >= thr) r = pinf;
+      S.lhs[i] = l;
+      S.rhs[i] = r;
+    }
+    if (i < Bp) {
+      S.node_rounds[i] = 0;
+      S.node_status[i] = 0;
+      S.node_done[i] = 1;
+    }
+    if (i < kMaxGroups) {
+      S.inf_bits[i] = 0u;
+      S.chg_bits[i] = 0u;
+      S.alive[i] = 0u;
+      S.fresh[i] = 0u;
+    }
+  }
+}
+
 int grid_for(int64_t work, int threads, int max_blocks) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -923,6 +1027,7 @@ cudaError_t launch_batch_prologue(const DevMatrix &M, const BatchState &S, int32
   const int64_t tiles = (((int64_t)M.n + 31) / 32) * (Bp / 32);
   int64_t total = M.n > M.m ? M.n : M.m;
   if (total < Bp) total = Bp;
+  if (total < kMaxGroups) total = kMaxGroups;
   k_bprologue_misc<<<grid_for(total, kThreads, num_sms * 16), kThreads, 0, st>>>(
       S, M.m, M.n, count, Bp, vartype, lhs, rhs, thr);
   cudaError_t e = cudaGetLastError();
@@ -978,6 +1083,39 @@ cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
   mark(10);
   k_bfinish<<<num_sms * 4, kThreads, 0, st>>>(S, M.n, handle, use_cond);
   mark(11);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slots_init(const DevMatrix &M, const BatchState &S, int32_t Bp,
+                              const uint8_t *vartype, const double *lhs, const double *rhs,
+                              double thr, int num_sms, cudaStream_t st) {
+  int64_t total = M.n > M.m ? M.n : M.m;
+  if (total < Bp) total = Bp;
+  if (total < kMaxGroups) total = kMaxGroups;
+  k_bslots_init<<<grid_for(total, kThreads, num_sms * 8), kThreads, 0, st>>>(S, M.m, M.n, Bp,
+                                                                             vartype, lhs, rhs, thr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slots_admit(const DevMatrix &M, const BatchState &S, int32_t Bp,
+                               const int32_t *slots, int32_t count, const double *stage,
+                               double eps_int, double eps_feas, double thr, int num_sms,
+                               cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_bslot_reset<<<(count + 127) / 128, 128, 0, st>>>(S, slots, count);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || M.n == 0) return e;
+  k_bslot_fill<<<grid_for((int64_t)count * M.n, kThreads, num_sms * 8), kThreads, 0, st>>>(
+      S, slots, count, stage, M.n, Bp, eps_int, eps_feas, thr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slots_extract(const DevMatrix &M, const BatchState &S, int32_t Bp,
+                                 const int32_t *slots, int32_t count, double *out,
+                                 int num_sms, cudaStream_t st) {
+  if (count <= 0 || M.n == 0) return cudaSuccess;
+  k_bslot_extract<<<grid_for((int64_t)count * M.n, kThreads, num_sms * 8), kThreads, 0, st>>>(
+      S, slots, count, out, M.n, Bp);
   return cudaGetLastError();
 }
 

@@ -16,49 +16,8 @@
 
 #include "dp_internal.h"
 #include "dp_launch.h"
+#include "dp_objects.h"
 #include "../../include/domprop.h"
-
-struct dp_ctx {
-  int device = 0;
-  int num_sms = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  dp::Ctrl *h_ctrl = nullptr;  // pinned mirror of the device control block
-  int live_matrices = 0;
-};
-
-struct dp_matrix {
-  dp_ctx *ctx = nullptr;
-  dp::DevMatrix M{};
-  dp::DevState S{};
-  int64_t padded = 0;
-  std::vector<void *> allocs;
-  uint8_t *vt_ws = nullptr;
-  // staging for host inputs / outputs
-  double *st_lb = nullptr, *st_ub = nullptr, *st_lhs = nullptr, *st_rhs = nullptr;
-  uint8_t *st_vt = nullptr;
-  double *out_lb = nullptr, *out_ub = nullptr;
-  // the round loop
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  // batched nodes (allocated on the first dp_propagate_nodes call)
-  struct BatchWs *batch = nullptr;
-};
-
-// Workspace of dp_propagate_nodes for up to Bp_cap nodes per launch.
-struct BatchWs {
-  int32_t Bp_cap = 0;
-  std::vector<void *> allocs;
-  dp::BatchState S{};
-  dp::BCtrl *h_ctrl = nullptr;  // pinned
-  int32_t *h_nodes = nullptr;   // pinned [3*Bp_cap]: infeasible, rounds, status
-  // staging of host inputs / outputs, allocated when first needed
-  double *st_lb = nullptr, *st_ub = nullptr, *out_lb = nullptr, *out_ub = nullptr;
-  double *st_lhs = nullptr, *st_rhs = nullptr;
-  uint8_t *st_vt = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-};
 
 namespace {
 
@@ -92,14 +51,7 @@ int upload(dp_matrix *mat, const std::vector<T> &v, const T **out, cudaStream_t 
   return DP_OK;
 }
 
-bool is_device_ptr(const void *p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+using dp::is_device_ptr;
 
 // Makes a round-loop graph: one WHILE node whose body is the kernels that
 // `body(handle, stream)` launches; the condition starts at 1 on every launch
@@ -494,6 +446,91 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
 
 // ------------------------------------------------------ batched B&B nodes --
 
+namespace dp {
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+template <typename T>
+int track_alloc(std::vector<void *> &allocs, T **p, size_t count, size_t *bytes) {
+  const size_t nb = sizeof(T) * (count > 0 ? count : 1);
+  if (bytes) {
+    *bytes += (nb + 255) & ~(size_t)255;
+    *p = nullptr;
+    return DP_OK;
+  }
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, nb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA;
+  }
+  allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return DP_OK;
+}
+
+// Allocates (or, with `bytes`, only sizes) the state of a batch.
+int batch_state(const DevMatrix &M, int32_t Bp, std::vector<void *> &allocs, BatchState &S,
+                size_t *bytes) {
+  const size_t n = (size_t)M.n, m = (size_t)M.m;
+  const size_t G = (size_t)Bp / 32, Gs = (G + 3) & ~(size_t)3;
+  const size_t nslots = (size_t)M.nslices * kSliceW;
+  const size_t split_slots = (size_t)M.nslices_split * kSliceW;
+  const size_t srows = (size_t)M.nsplit_rows;
+  int rc;
+#define ATRY(x) \
+  if ((rc = (x)) != DP_OK) return rc
+  ATRY(track_alloc(allocs, &S.cur, n * Bp, bytes));
+  ATRY(track_alloc(allocs, &S.nkey, 2 * n * Bp, bytes));
+  ATRY(track_alloc(allocs, &S.chg[0], n * Gs, bytes));
+  ATRY(track_alloc(allocs, &S.chg[1], n * Gs, bytes));
+  ATRY(track_alloc(allocs, &S.dirty[0], 2 * n * Bp, bytes));
+  ATRY(track_alloc(allocs, &S.dirty[1], 2 * n * Bp, bytes));
+  ATRY(track_alloc(allocs, &S.cmask, nslots * Gs, bytes));
+  ATRY(track_alloc(allocs, &S.items, G * nslots, bytes));
+  ATRY(track_alloc(allocs, &S.part, split_slots * Bp, bytes));
+  ATRY(track_alloc(allocs, &S.rowtot, srows * Bp, bytes));
+  ATRY(track_alloc(allocs, &S.srow_act, srows * Gs, bytes));
+  ATRY(track_alloc(allocs, &S.inf_bits, (size_t)kMaxGroups, bytes));
+  ATRY(track_alloc(allocs, &S.chg_bits, (size_t)kMaxGroups, bytes));
+  ATRY(track_alloc(allocs, &S.node_rounds, (size_t)Bp, bytes));
+  ATRY(track_alloc(allocs, &S.node_status, (size_t)Bp, bytes));
+  ATRY(track_alloc(allocs, &S.node_done, (size_t)Bp, bytes));
+  ATRY(track_alloc(allocs, &S.alive, (size_t)kMaxGroups, bytes));
+  ATRY(track_alloc(allocs, &S.fresh, (size_t)kMaxGroups, bytes));
+  ATRY(track_alloc(allocs, &S.lhs, m, bytes));
+  ATRY(track_alloc(allocs, &S.rhs, m, bytes));
+  ATRY(track_alloc(allocs, &S.vt, n, bytes));
+  ATRY(track_alloc(allocs, &S.ctrl, 1, bytes));
+#undef ATRY
+  S.nslots = (int64_t)nslots;
+  return DP_OK;
+}
+}  // namespace
+
+int alloc_batch_state(const DevMatrix &M, int32_t Bp, std::vector<void *> &allocs,
+                      BatchState &S) {
+  return batch_state(M, Bp, allocs, S, nullptr);
+}
+
+size_t batch_state_bytes(const DevMatrix &M, int32_t Bp) {
+  std::vector<void *> none;
+  BatchState S{};
+  size_t bytes = 0;
+  batch_state(M, Bp, none, S, &bytes);
+  return bytes;
+}
+
+}  // namespace dp
+
 namespace {
 
 template <typename T>
@@ -533,12 +570,6 @@ int ensure_batch(dp_matrix *mat, int32_t Bp) {
   }
   BatchWs *b = new (std::nothrow) BatchWs();
   if (!b) return DP_ERR_OOM;
-  const dp::DevMatrix &M = mat->M;
-  const size_t n = (size_t)M.n, m = (size_t)M.m;
-  const size_t G = (size_t)Bp / 32, Gs = (G + 3) & ~(size_t)3;
-  const size_t nslots = (size_t)M.nslices * dp::kSliceW;
-  const size_t split_slots = (size_t)M.nslices_split * dp::kSliceW;
-  const size_t srows = (size_t)M.nsplit_rows;
   dp::BatchState &S = b->S;
   int rc = DP_OK;
 #define BTRY(x)                 \
@@ -548,28 +579,7 @@ int ensure_batch(dp_matrix *mat, int32_t Bp) {
       return rc;                \
     }                           \
   } while (0)
-  BTRY(batch_alloc(b, &S.cur, n * Bp));
-  BTRY(batch_alloc(b, &S.nkey, 2 * n * Bp));
-  BTRY(batch_alloc(b, &S.chg[0], n * Gs));
-  BTRY(batch_alloc(b, &S.chg[1], n * Gs));
-  BTRY(batch_alloc(b, &S.dirty[0], 2 * n * Bp));
-  BTRY(batch_alloc(b, &S.dirty[1], 2 * n * Bp));
-  BTRY(batch_alloc(b, &S.cmask, nslots * Gs));
-  BTRY(batch_alloc(b, &S.items, G * nslots));
-  BTRY(batch_alloc(b, &S.part, split_slots * Bp));
-  BTRY(batch_alloc(b, &S.rowtot, srows * Bp));
-  BTRY(batch_alloc(b, &S.srow_act, srows * Gs));
-  BTRY(batch_alloc(b, &S.inf_bits, (size_t)dp::kMaxGroups));
-  BTRY(batch_alloc(b, &S.chg_bits, (size_t)dp::kMaxGroups));
-  BTRY(batch_alloc(b, &S.node_rounds, (size_t)Bp));
-  BTRY(batch_alloc(b, &S.node_status, (size_t)Bp));
-  BTRY(batch_alloc(b, &S.node_done, (size_t)Bp));
-  BTRY(batch_alloc(b, &S.alive, (size_t)dp::kMaxGroups));
-  BTRY(batch_alloc(b, &S.lhs, m));
-  BTRY(batch_alloc(b, &S.rhs, m));
-  BTRY(batch_alloc(b, &S.vt, n));
-  BTRY(batch_alloc(b, &S.ctrl, 1));
-  S.nslots = (int64_t)nslots;
+  BTRY(dp::alloc_batch_state(mat->M, Bp, b->allocs, S));
   if (cudaMallocHost(&b->h_ctrl, sizeof(dp::BCtrl)) != cudaSuccess ||
       cudaMallocHost(&b->h_nodes, sizeof(int32_t) * 3 * (size_t)Bp) != cudaSuccess) {
     cudaGetLastError();

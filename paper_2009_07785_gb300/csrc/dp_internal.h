@@ -172,6 +172,7 @@ struct BatchState {
   int32_t *node_status; // [Bp] 1 = stopped by the round cap
   int32_t *node_done;   // [Bp]
   uint32_t *alive;      // [G] nodes still propagating
+  uint32_t *fresh;      // [kMaxGroups] nodes in their first round (every row active)
   double *lhs, *rhs;    // [m] normalised sides
   uint8_t *vt;          // [n] 0/1 variable types
   BCtrl *ctrl;

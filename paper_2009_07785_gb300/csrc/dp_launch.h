@@ -46,6 +46,24 @@ cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
                                cudaGraphConditionalHandle handle, int use_cond,
                                int num_sms, cudaStream_t st, cudaEvent_t *ev);
 
+// Serving slots (dp_batch.cu): a batch whose nodes are independent requests.
+// launch_slots_init writes the sides and types and leaves every slot empty;
+// launch_slots_admit resets the per-node state of `count` slots (device
+// array `slots`) and fills their bounds from `stage` (slot i: lb at
+// stage + 2*i*n, ub at stage + (2*i+1)*n, validated by the host);
+// launch_slots_extract copies the bounds of `count` slots to `out` in the
+// same layout.
+cudaError_t launch_slots_init(const DevMatrix &M, const BatchState &S, int32_t Bp,
+                              const uint8_t *vartype, const double *lhs, const double *rhs,
+                              double thr, int num_sms, cudaStream_t st);
+cudaError_t launch_slots_admit(const DevMatrix &M, const BatchState &S, int32_t Bp,
+                               const int32_t *slots, int32_t count, const double *stage,
+                               double eps_int, double eps_feas, double thr, int num_sms,
+                               cudaStream_t st);
+cudaError_t launch_slots_extract(const DevMatrix &M, const BatchState &S, int32_t Bp,
+                                 const int32_t *slots, int32_t count, double *out,
+                                 int num_sms, cudaStream_t st);
+
 // Host image of the device layout described in dp_internal.h.
 struct HostLayout {
   int32_t m = 0, n = 0;
