@@ -18,6 +18,9 @@ cpu_baseline / --impl reference: the CPU oracle (one thread) on a bounded
 batched_nodes: 256 branch-and-bound node bound vectors over the medium
           matrix (m=200k, ~2M nonzeros) propagated by one dp_propagate_nodes
           call, against the plain loop of one dp_propagate call per node.
+serving:  Poisson request streams (1k..50k requests/s) over 32 resident
+          matrices (nonzeros log-uniform 1e3..1e6) through dp_server_*:
+          p50/p99 latency from arrival to result and achieved requests/s.
 
 Multi-GPU (torchrun): replicas -- every rank propagates its own copy of the
 workload; there is no data-path collective (scaling: weak).
@@ -62,6 +65,10 @@ def parse():
     ap.add_argument("--nodes-only", action="store_true",
                     help="run only the batched node measurement (profiling captures)")
     ap.add_argument("--nodes-count", type=int, default=256)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving (continuous batching) measurement")
+    ap.add_argument("--serving-only", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -305,6 +312,81 @@ def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3):
     return out
 
 
+def serving_pool(count=32, seed_k=0):
+    """32 resident matrices like the medium workload with nonzeros
+    log-uniform in 1e3..1e6 (seeded), and per matrix a set of node bound
+    vectors (fixings at the feasible point's values)."""
+    from paper_2009_07785_gb300 import synth
+
+    rng = np.random.default_rng(synth.seed_for(4, seed_k))
+    target = np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=count))
+    insts = [synth.medium(seed=synth.seed_for(4, 1 + k), scale=float(t) / 2.0e6)
+             for k, t in enumerate(target)]
+    nodes = [synth.node_bounds_at_point(inst, 16, seed=synth.seed_for(4, 100 + k))
+             for k, inst in enumerate(insts)]
+    return insts, nodes
+
+
+def serving_bench(dp, ctx, rates=(1000, 5000, 10000, 20000, 50000), seconds=1.0,
+                  slots=64, max_requests=20000):
+    """Poisson request streams over the resident pool: each request is a
+    random pool matrix and one of its node bound vectors; requests are
+    submitted at their arrival times (the submitting loop waits for each);
+    latency = completion time - arrival time on the server's clock."""
+    pool_insts, pool_nodes = serving_pool()
+    mats = [dp.Matrix(ctx, i.m, i.n, i.row_ptr, i.col, i.val) for i in pool_insts]
+    out = {"pool": f"{len(mats)} matrices like the medium workload, nonzeros "
+                   f"{min(i.nnz for i in pool_insts)}..{max(i.nnz for i in pool_insts)} "
+                   f"(log-uniform), 16 node vectors each (1-5% integer fixings at x*)",
+           "slots_per_matrix": slots, "rates": []}
+    rng = np.random.default_rng(12345)
+    for rate in rates:
+        nreq = int(min(max_requests, rate * seconds))
+        with dp.Server(ctx, slots=slots) as srv:
+            ids = [srv.add_matrix(m, i.vartype, i.lhs, i.rhs) for m, i in zip(mats, pool_insts)]
+            # warm-up: one request per matrix (workspaces, graphs)
+            for k, mid in enumerate(ids):
+                srv.submit(mid, pool_nodes[k][0][0], pool_nodes[k][1][0])
+            got = 0
+            while got < len(ids):
+                got += len(srv.poll(256, wait_us=5000))
+            gaps = rng.exponential(1e6 / rate, size=nreq)
+            which = rng.integers(0, len(ids), size=nreq)
+            vec = rng.integers(0, 16, size=nreq)
+            outs = [(np.empty(pool_insts[k].n), np.empty(pool_insts[k].n)) for k in range(len(ids))]
+            t0 = dp.dp_server_clock_us() + 2000.0
+            arrival = t0 + np.cumsum(gaps)
+            lat, rounds, done = [], 0, 0
+            for q in range(nreq):
+                while dp.dp_server_clock_us() < arrival[q]:
+                    pass
+                k = int(which[q])
+                srv.submit(ids[k], pool_nodes[k][0][vec[q]], pool_nodes[k][1][vec[q]],
+                           outs[k][0], outs[k][1], arrival_us=float(arrival[q]))
+                if q % 64 == 0:
+                    for c in srv.poll(1024):
+                        lat.append(c["done_us"] - c["arrival_us"])
+                        rounds += c["rounds"]
+            while len(lat) < nreq:
+                for c in srv.poll(1024, wait_us=10000):
+                    lat.append(c["done_us"] - c["arrival_us"])
+                    rounds += c["rounds"]
+            t_end = dp.dp_server_clock_us()
+            st = srv.stats()
+        lat = np.asarray(lat)
+        span_s = (t_end - arrival[0]) * 1e-6
+        out["rates"].append({"offered_req_per_s": rate, "requests": nreq,
+                             "achieved_req_per_s": nreq / span_s,
+                             "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                             "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                             "mean_rounds": rounds / nreq,
+                             "mean_active_slots": st["slot_rounds"] / max(st["rounds"], 1),
+                             "max_active_slots": st["max_active_slots"]})
+    for m in mats:
+        m.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -323,6 +405,11 @@ def run_ours(args):
         ctx = dp.Context(local, torch.cuda.current_stream())
         print(json.dumps({"batched_nodes": nodes_bench(dp, ctx, torch.cuda.current_stream(),
                                                        count=args.nodes_count)}))
+        ctx.close()
+        return 0
+    if args.serving_only:
+        ctx = dp.Context(local, torch.cuda.current_stream())
+        print(json.dumps({"serving": serving_bench(dp, ctx, seconds=args.serving_seconds)}))
         ctx.close()
         return 0
     inst = make_workload(args.workload, args.scale)
@@ -419,6 +506,9 @@ def run_ours(args):
     nodes = None
     if ws == 1 and not args.no_nodes:
         nodes = nodes_bench(dp, ctx, stream, count=args.nodes_count)
+    serving = None
+    if ws == 1 and not args.no_serving:
+        serving = serving_bench(dp, ctx, seconds=args.serving_seconds)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -434,7 +524,7 @@ def run_ours(args):
                           "l2": "no flush: the matrix streamed each round (0.36 GB) exceeds the 129 MB L2",
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk, "batched_nodes": nodes}
+               "clocks": clk, "batched_nodes": nodes, "serving": serving}
         print(json.dumps(out))
     mat.close()
     ctx.close()
