@@ -18,23 +18,46 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 __device__ __forceinline__ float f_inf() { return __uint_as_float(0x7F800000u); }
 
+// The two 32-bit halves of a binary64 value through an opaque register move,
+// so that the tests below stay integer operations.  Written as plain bit
+// tests on the 64-bit pattern, some of them are recognised by the compiler
+// as binary64 comparisons (class tests), which issue on the binary64 pipe:
+// one per test, i.e. as many as the activity FMAs in the activity loop.
+__device__ __forceinline__ void dsplit(double x, unsigned &lo, unsigned &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+}
 __device__ __forceinline__ bool d_isinf(double x) {
-  return ((unsigned long long)__double_as_longlong(x) << 1) == 0xFFE0000000000000ull;
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  return ((hi & 0x7FFFFFFFu) == 0x7FF00000u) & (lo == 0u);
 }
 __device__ __forceinline__ bool d_isfinite(double x) {
-  return ((__double2hiint(x) >> 20) & 0x7FF) != 0x7FF;
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  return (hi & 0x7FF00000u) != 0x7FF00000u;
 }
 __device__ __forceinline__ bool d_isnan(double x) {
-  return ((unsigned long long)__double_as_longlong(x) << 1) > 0xFFE0000000000000ull;
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  const unsigned h = hi & 0x7FFFFFFFu;
+  return (h > 0x7FF00000u) | ((h == 0x7FF00000u) & (lo != 0u));
 }
 __device__ __forceinline__ bool d_is_neginf(double x) {
-  return (unsigned long long)__double_as_longlong(x) == 0xFFF0000000000000ull;
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  return (hi == 0xFFF00000u) & (lo == 0u);
 }
 __device__ __forceinline__ bool d_is_posinf(double x) {
-  return (unsigned long long)__double_as_longlong(x) == 0x7FF0000000000000ull;
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  return (hi == 0x7FF00000u) & (lo == 0u);
 }
-// coefficient sign without an FP64 comparison (coefficients are nonzero)
-__device__ __forceinline__ bool d_pos(double a) { return __double2hiint(a) >= 0; }
+// coefficient sign without a binary64 comparison (coefficients are nonzero)
+__device__ __forceinline__ bool d_pos(double a) {
+  unsigned lo, hi;
+  dsplit(a, lo, hi);
+  return (int)hi >= 0;
+}
 
 // Order-preserving map between binary64 values and signed 64-bit keys, so
 // that integer atomicMax/atomicMin implement max/min of doubles.
