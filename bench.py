@@ -415,7 +415,8 @@ def run_ours(args):
     inst = make_workload(args.workload, args.scale)
     stream = torch.cuda.current_stream()
     ctx = dp.Context(local, stream)
-    mat = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, args.chunk)
+    mat = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, args.chunk,
+                    lhs=inst.lhs, rhs=inst.rhs)
     info = mat.info()
     d_in = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in inst.problem()]
     d_lb = torch.empty(inst.n, dtype=torch.float64, device="cuda")

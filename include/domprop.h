@@ -119,6 +119,21 @@ int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                    const int64_t *row_ptr, const int32_t *col_idx,
                    const double *val, int32_t chunk, dp_matrix **out);
 
+/*
+ * dp_matrix_load with the row sides known at load time (HOST lhs[m],
+ * rhs[m]; not kept).  They only order rows of equal length by which sides
+ * are finite (|side| < 1e20), so that the 32 rows of a warp tend to share
+ * a side pattern and a warp whose rows all have an infinite side skips that
+ * side's activity (its binary64 work halves for one-sided rows).  Any
+ * dp_propagate call on the matrix stays valid with any sides: the kernels
+ * test the actual sides.  The paper has no counterpart (its rows are
+ * grouped by length only, Sec. 3.2).
+ */
+int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col_idx,
+                         const double *val, int32_t chunk, const double *lhs,
+                         const double *rhs, dp_matrix **out);
+
 /* Frees a matrix; NULL is a no-op. */
 void dp_matrix_free(dp_matrix *mat);
 

@@ -30,7 +30,7 @@ DP_ERR_TIMEOUT = -6
 
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
-           "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
+           "dp_matrix_load_sides", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
            "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
@@ -82,6 +82,8 @@ def lib() -> C.CDLL:
     L.dp_destroy.restype = None
     L.dp_matrix_load.argtypes = [vp, i32, i32, i64, vp, vp, vp, i32, C.POINTER(vp)]
     L.dp_matrix_load.restype = C.c_int
+    L.dp_matrix_load_sides.argtypes = [vp, i32, i32, i64, vp, vp, vp, i32, vp, vp, C.POINTER(vp)]
+    L.dp_matrix_load_sides.restype = C.c_int
     L.dp_matrix_free.argtypes = [vp]
     L.dp_matrix_free.restype = None
     L.dp_matrix_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
@@ -197,14 +199,25 @@ def dp_destroy(ctx: Context) -> None:
 class Matrix:
     """A dp_matrix: a CSR constraint matrix resident on the GPU."""
 
-    def __init__(self, ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int = 0):
+    def __init__(self, ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int = 0,
+                 lhs=None, rhs=None):
+        """lhs/rhs (optional, host): the row sides known at load time, used
+        only to order rows by side pattern (dp_matrix_load_sides)."""
         row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
         val = np.ascontiguousarray(val, dtype=np.float64)
         h = C.c_void_p()
-        _check(lib().dp_matrix_load(ctx.handle, int(m), int(n), int(row_ptr[-1]) if m > 0 else 0,
-                                    _ptr(row_ptr), _ptr(col_idx), _ptr(val), int(chunk),
-                                    C.byref(h)), "dp_matrix_load")
+        nnz = int(row_ptr[-1]) if m > 0 else 0
+        if lhs is None and rhs is None:
+            _check(lib().dp_matrix_load(ctx.handle, int(m), int(n), nnz, _ptr(row_ptr),
+                                        _ptr(col_idx), _ptr(val), int(chunk), C.byref(h)),
+                   "dp_matrix_load")
+        else:
+            lhs = np.ascontiguousarray(lhs, dtype=np.float64)
+            rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+            _check(lib().dp_matrix_load_sides(ctx.handle, int(m), int(n), nnz, _ptr(row_ptr),
+                                              _ptr(col_idx), _ptr(val), int(chunk), _ptr(lhs),
+                                              _ptr(rhs), C.byref(h)), "dp_matrix_load_sides")
         self.handle = h
         self.ctx = ctx
         self.m, self.n = int(m), int(n)
@@ -231,6 +244,11 @@ class Matrix:
 
 def dp_matrix_load(ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int = 0) -> Matrix:
     return Matrix(ctx, m, n, row_ptr, col_idx, val, chunk)
+
+
+def dp_matrix_load_sides(ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int,
+                         lhs, rhs) -> Matrix:
+    return Matrix(ctx, m, n, row_ptr, col_idx, val, chunk, lhs, rhs)
 
 
 def dp_matrix_free(mat: Matrix) -> None:

@@ -213,10 +213,19 @@ void dp_matrix_free(dp_matrix *mat) {
 int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                    const int64_t *row_ptr, const int32_t *col_idx,
                    const double *val, int32_t chunk, dp_matrix **out) {
+  return dp_matrix_load_sides(ctx, m, n, nnz, row_ptr, col_idx, val, chunk, nullptr, nullptr,
+                              out);
+}
+
+int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col_idx, const double *val,
+                         int32_t chunk, const double *lhs, const double *rhs,
+                         dp_matrix **out) {
   if (!ctx || !out) return DP_ERR_INVALID_ARG;
   *out = nullptr;
+  if ((lhs == nullptr) != (rhs == nullptr)) return DP_ERR_INVALID_ARG;
   dp::HostLayout H;
-  int rc = dp::build_layout(m, n, nnz, row_ptr, col_idx, val, chunk, H);
+  int rc = dp::build_layout(m, n, nnz, row_ptr, col_idx, val, chunk, lhs, rhs, H);
   if (rc) return rc;
   CUDA_TRY(cudaSetDevice(ctx->device));
   dp_matrix *mat = new (std::nothrow) dp_matrix();

@@ -265,6 +265,14 @@ k_round(DevMatrix M, DevState S) {
   const double *vp = svp + lane;
   const int32_t *cp = scp + lane;
 
+  // A side's activity is needed only by rows whose side is finite (Step 2
+  // and the candidates of that side); a warp skips the activity no lane
+  // needs (warp-uniform: rows are ordered by side pattern when the sides
+  // are known at load time).
+  const double2 sd = (row >= 0) ? S.side[c] : make_double2(0.0, 0.0);  // slot order
+  const bool need_min = __any_sync(kFull, row >= 0 && d_isfinite(sd.y));
+  const bool need_max = __any_sync(kFull, row >= 0 && d_isfinite(sd.x));
+
   // ---- activities of the chunk (Def. 1, Eq. 2a/2b; Sec. 3.4) ----
   double minfin = 0.0, maxfin = 0.0;
   int32_t mininf = 0, maxinf = 0;
@@ -311,18 +319,23 @@ k_round(DevMatrix M, DevState S) {
     for (int u = 0; u < kGroup; ++u) {
       if (k + u < len) {
         bool pos = d_pos(a[u]);
-        double bmin = pos ? L[u] : U[u];
-        double bmax = pos ? U[u] : L[u];
-        bool imin = d_isinf(bmin), imax = d_isinf(bmax);
-        mininf += imin;
-        maxinf += imax;
-        if (imin) t.kinf_min = k + u;
-        if (imax) t.kinf_max = k + u;
-        minfin = fma(a[u], imin ? 0.0 : bmin, minfin);
-        maxfin = fma(a[u], imax ? 0.0 : bmax, maxfin);
         float au = absup_fast(a[u]);
-        top2_add(__fmul_ru(au, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
-        top2_add(__fmul_ru(au, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
+        if (need_min) {
+          double bmin = pos ? L[u] : U[u];
+          bool imin = d_isinf(bmin);
+          mininf += imin;
+          if (imin) t.kinf_min = k + u;
+          minfin = fma(a[u], imin ? 0.0 : bmin, minfin);
+          top2_add(__fmul_ru(au, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
+        }
+        if (need_max) {
+          double bmax = pos ? U[u] : L[u];
+          bool imax = d_isinf(bmax);
+          maxinf += imax;
+          if (imax) t.kinf_max = k + u;
+          maxfin = fma(a[u], imax ? 0.0 : bmax, maxfin);
+          top2_add(__fmul_ru(au, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
+        }
       }
     }
   }
@@ -354,7 +367,6 @@ k_round(DevMatrix M, DevState S) {
   rv.act = 0;
   rv.thr_r = rv.thr_l = f_inf();
   if (row >= 0) {
-    const double2 sd = S.side[c];  // coalesced: sides stored in slot order
     rv.lhs = sd.x;
     rv.rhs = sd.y;
     row_sides(rv, t.r1, t.l1, ctrl->eps_feas, &S.ctrl->infeasible);

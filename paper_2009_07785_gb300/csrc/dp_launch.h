@@ -77,10 +77,12 @@ struct HostLayout {
   std::vector<int32_t> split_row, split_cbeg, split_cidx;
 };
 
-// Validates a host CSR matrix and builds its layout.  Returns DP_OK,
-// DP_ERR_INVALID_ARG, DP_ERR_BAD_CSR or DP_ERR_OOM.
+// Validates a host CSR matrix and builds its layout; lhs_hint/rhs_hint
+// (host, may be NULL) only order rows of equal length by the finiteness of
+// their sides.  Returns DP_OK, DP_ERR_INVALID_ARG, DP_ERR_BAD_CSR or
+// DP_ERR_OOM.
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
                  const int32_t *col_idx, const double *val, int32_t chunk,
-                 HostLayout &out);
+                 const double *lhs_hint, const double *rhs_hint, HostLayout &out);
 
 }  // namespace dp

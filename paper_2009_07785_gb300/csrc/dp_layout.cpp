@@ -32,9 +32,23 @@ struct Chunk {
 
 }  // namespace
 
+namespace {
+// Side class of a row for the ordering within one chunk length: rows whose
+// sides have the same finiteness share warps, so a warp whose rows all have
+// an infinite side skips that side's activity.  0: both sides finite,
+// 1: only rhs finite, 2: only lhs finite, 3: neither.  Without hints every
+// row is class 0.
+int side_class(const double *lhs, const double *rhs, int32_t i) {
+  if (!lhs || !rhs) return 0;
+  const double thr = 1e20;
+  const bool fl = std::fabs(lhs[i]) < thr, fr = std::fabs(rhs[i]) < thr;
+  return fl ? (fr ? 0 : 2) : (fr ? 1 : 3);
+}
+}  // namespace
+
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
                  const int32_t *col_idx, const double *val, int32_t chunk,
-                 HostLayout &out) {
+                 const double *lhs_hint, const double *rhs_hint, HostLayout &out) {
   if (m < 0 || n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return DP_ERR_INVALID_ARG;
   if (m > 0 && !row_ptr) return DP_ERR_INVALID_ARG;
   if (nnz > 0 && (!col_idx || !val)) return DP_ERR_INVALID_ARG;
@@ -85,14 +99,17 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     // each split row's pieces to their slots
     {
       const size_t ns = chunks.size();
-      std::vector<size_t> cnt2((size_t)chunk + 2, 0);
-      for (const Chunk &ch : chunks) cnt2[(size_t)(chunk - ch.len)]++;
-      std::vector<size_t> at2((size_t)chunk + 2, 0);
+      auto key2 = [&](const Chunk &ch) {
+        return (size_t)(chunk - ch.len) * 4 + (size_t)side_class(lhs_hint, rhs_hint, ch.row);
+      };
+      std::vector<size_t> cnt2(((size_t)chunk + 2) * 4, 0);
+      for (const Chunk &ch : chunks) cnt2[key2(ch)]++;
+      std::vector<size_t> at2(cnt2.size(), 0);
       for (size_t b = 1; b < at2.size(); ++b) at2[b] = at2[b - 1] + cnt2[b - 1];
       std::vector<Chunk> sorted(ns);
       out.split_cidx.assign(ns, 0);
       for (size_t q = 0; q < ns; ++q) {
-        size_t slot = at2[(size_t)(chunk - chunks[q].len)]++;
+        size_t slot = at2[key2(chunks[q])]++;
         sorted[slot] = chunks[q];
         out.split_cidx[q] = (int32_t)slot;
       }
@@ -102,20 +119,24 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     while (chunks.size() % kSliceW) chunks.push_back({-1, 0, 0, 0, -1});
     const size_t nsplit_chunks = chunks.size();
 
-    // single-chunk rows by length, longest first (counting sort, stable)
-    std::vector<int64_t> cnt((size_t)chunk + 2, 0);
+    // single-chunk rows by length, longest first, then by side class
+    // (counting sort, stable)
+    auto key1 = [&](int32_t i, int64_t len) {
+      return (size_t)(chunk - len) * 4 + (size_t)side_class(lhs_hint, rhs_hint, i);
+    };
+    std::vector<int64_t> cnt(((size_t)chunk + 2) * 4, 0);
     for (int32_t i = 0; i < m; ++i) {
       int64_t len = row_ptr[i + 1] - row_ptr[i];
-      if (len <= chunk) cnt[(size_t)(chunk - len)]++;
+      if (len <= chunk) cnt[key1(i, len)]++;
     }
-    std::vector<int64_t> pos((size_t)chunk + 2, 0);
+    std::vector<int64_t> pos(cnt.size(), 0);
     for (size_t b = 1; b < pos.size(); ++b) pos[b] = pos[b - 1] + cnt[b - 1];
-    size_t nsingle = (size_t)pos.back();
+    size_t nsingle = (size_t)(pos.back() + cnt.back());
     chunks.resize(nsplit_chunks + nsingle);
     for (int32_t i = 0; i < m; ++i) {
       int64_t len = row_ptr[i + 1] - row_ptr[i];
       if (len > chunk) continue;
-      size_t at = nsplit_chunks + (size_t)pos[(size_t)(chunk - len)]++;
+      size_t at = nsplit_chunks + (size_t)pos[key1(i, len)]++;
       chunks[at] = {i, row_ptr[i], (int32_t)len, rowflag[i], -1};
     }
     while (chunks.size() % kSliceW) chunks.push_back({-1, 0, 0, 0, -1});

@@ -134,3 +134,40 @@ def test_large_scaled(gpu, orc):
         assert mat.info()["split_rows"] > 0
         replay(dp, ctx, mat, inst, orc)
         check_full(dp, ctx, mat, inst, orc, exact=False)
+
+
+def test_side_ordered_layout_bit_exact(gpu, orc):
+    """Rows ordered by side pattern (dp_matrix_load_sides): warps whose rows
+    all have an infinite side skip that side's activity; results unchanged."""
+    dp, ctx = gpu
+    inst = synth.tiny()
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
+                   lhs=inst.lhs, rhs=inst.rhs) as mat:
+        check_full(dp, ctx, mat, inst, orc, exact=True)
+        rounds, ties = replay(dp, ctx, mat, inst, orc)
+        assert ties == 0
+
+
+@pytest.mark.parametrize("chunk", [0, 16])
+def test_side_hints_never_change_results(gpu, orc, chunk):
+    """Hints that disagree with the sides of the call (finite where the call
+    has infinite sides and the reverse) change the order only."""
+    dp, ctx = gpu
+    rng = np.random.default_rng(23)
+    inst = synth.small_random(rng, 600, 500, 40, ranged_frac=0.5)
+    wrong_l = np.where(np.isfinite(inst.lhs), -np.inf, 0.0)
+    wrong_r = np.where(np.isfinite(inst.rhs), np.inf, 0.0)
+    for hl, hr in ((inst.lhs, inst.rhs), (wrong_l, wrong_r)):
+        with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, chunk,
+                       lhs=hl, rhs=hr) as mat:
+            replay(dp, ctx, mat, inst, orc)
+            check_full(dp, ctx, mat, inst, orc, exact=(chunk == 0))
+
+
+def test_large_scaled_side_ordered(gpu, orc):
+    dp, ctx = gpu
+    inst = synth.large(scale=0.02)
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
+                   lhs=inst.lhs, rhs=inst.rhs) as mat:
+        replay(dp, ctx, mat, inst, orc)
+        check_full(dp, ctx, mat, inst, orc, exact=False)
