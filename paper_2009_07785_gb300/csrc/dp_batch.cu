@@ -173,9 +173,9 @@ __device__ __forceinline__ void act_add(double a, double2 b, uint8_t t, bool nee
   if (screen) {
     float WU, WL;
     screen_widths(b.x, b.y, t != 0, P.tau_dn, P.eps_dn, WU, WL);
-    const float au = absup_fast(a);
-    if (need_min) r.tr = fmaxf(r.tr, __fmul_ru(au, pos ? WU : WL));
-    if (need_max) r.tl = fmaxf(r.tl, __fmul_ru(au, pos ? WL : WU));
+    const float au = absup_fast(a), ad = absdn_fast(a);
+    if (need_min) r.tr = fmaxf(r.tr, screen_prod(au, ad, pos ? WU : WL));
+    if (need_max) r.tl = fmaxf(r.tl, screen_prod(au, ad, pos ? WL : WU));
   }
 }
 

@@ -153,6 +153,18 @@ __device__ __forceinline__ float absup_fast(double a) {
   unsigned t = ((mh << 3) | (lo >> 29)) - (896u << 23);
   return __uint_as_float(t + ((lo & 0x1FFFFFFFu) != 0u));
 }
+// Lower bound on |a| as binary32 (truncated significand), same range.
+__device__ __forceinline__ float absdn_fast(double a) {
+  unsigned lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(a));
+  const unsigned mh = hi & 0x7FFFFFFFu;
+  return __uint_as_float(((mh << 3) | (lo >> 29)) - (896u << 23));
+}
+// Upper bound on |a| * W from |a| in [ad, au] and an upper bound W of the
+// width (either sign).
+__device__ __forceinline__ float screen_prod(float au, float ad, float W) {
+  return __fmul_ru(W >= 0.0f ? au : ad, W);
+}
 
 // ---- the binary32 screen ---------------------------------------------------
 //
@@ -166,11 +178,14 @@ __device__ __forceinline__ float absup_fast(double a) {
 //   right-hand side: a > 0 -> upper (WU), a < 0 -> lower (WL)
 //   left-hand side:  a > 0 -> lower (WL), a < 0 -> upper (WU)
 // The record stores binary32 upper bounds of WU, WL enlarged by
-// 2^-40 (|L|+|U|), clamped at 0; a row side stores a binary32 lower bound
-// thr of s - 2^-39 (|side| + |activity|).  These margins exceed the rounding
-// of every binary64 operation of the candidate formula and of the
-// acceptance threshold, so  upper(|a|) * W <= thr  proves that the
-// nonzero's candidate from that side is not applied.
+// 2^-40 (|L|+|U|); a row side stores a binary32 lower bound thr of
+// s - 2^-39 (|side| + |activity|).  These margins exceed the rounding of
+// every binary64 operation of the candidate formula and of the acceptance
+// threshold, so  upper(|a| W) <= thr  proves that the nonzero's candidate
+// from that side is not applied.  W may be negative (a fixed variable, or
+// bounds closer than the threshold): then |a| W <= lower(|a|) * upper(W),
+// which keeps the candidates of fixed variables in tight rows (zero slack,
+// e.g. set partitioning rows at the fixed point) out of the exact path.
 
 __device__ __forceinline__ void screen_widths(double L, double U, bool isint, float tau_dn,
                                               float eps_dn, float &WU, float &WL) {
@@ -187,8 +202,8 @@ __device__ __forceinline__ void screen_widths(double L, double U, bool isint, fl
     cu = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn_abs(U)));
     cl = __fmul_rd(tau_dn, fmaxf(1.0f, f32_dn_abs(L)));
   }
-  WU = fmaxf(__fadd_ru(__fsub_ru(base, cu), absorb), 0.0f);
-  WL = fmaxf(__fadd_ru(__fsub_ru(base, cl), absorb), 0.0f);
+  WU = __fadd_ru(__fsub_ru(base, cu), absorb);
+  WL = __fadd_ru(__fsub_ru(base, cl), absorb);
   if (!(WU == WU)) WU = f_inf();  // never NaN (inf - inf on invalid input)
   if (!(WL == WL)) WL = f_inf();
 }
@@ -290,9 +305,9 @@ __device__ __forceinline__ unsigned nnz_sides(double a, double L, double U, floa
   bool pos = d_pos(a);
   double bmin = pos ? L : U;
   double bmax = pos ? U : L;
-  float au = absup_fast(a);
-  float tr = rv.exact ? f_inf() : __fmul_ru(au, pos ? WU : WL);
-  float tl = rv.exact ? f_inf() : __fmul_ru(au, pos ? WL : WU);
+  float au = absup_fast(a), ad = absdn_fast(a);
+  float tr = rv.exact ? f_inf() : screen_prod(au, ad, pos ? WU : WL);
+  float tl = rv.exact ? f_inf() : screen_prod(au, ad, pos ? WL : WU);
   bool r = d_isfinite(rv.rhs) &&
            ((rv.mininf == 0 && tr > rv.thr_r) || (rv.mininf == 1 && d_isinf(bmin)));
   bool l = d_isfinite(rv.lhs) &&

@@ -319,14 +319,14 @@ k_round(DevMatrix M, DevState S) {
     for (int u = 0; u < kGroup; ++u) {
       if (k + u < len) {
         bool pos = d_pos(a[u]);
-        float au = absup_fast(a[u]);
+        float au = absup_fast(a[u]), ad = absdn_fast(a[u]);
         if (need_min) {
           double bmin = pos ? L[u] : U[u];
           bool imin = d_isinf(bmin);
           mininf += imin;
           if (imin) t.kinf_min = k + u;
           minfin = fma(a[u], imin ? 0.0 : bmin, minfin);
-          top2_add(__fmul_ru(au, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
+          top2_add(screen_prod(au, ad, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
         }
         if (need_max) {
           double bmax = pos ? U[u] : L[u];
@@ -334,7 +334,7 @@ k_round(DevMatrix M, DevState S) {
           maxinf += imax;
           if (imax) t.kinf_max = k + u;
           maxfin = fma(a[u], imax ? 0.0 : bmax, maxfin);
-          top2_add(__fmul_ru(au, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
+          top2_add(screen_prod(au, ad, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
         }
       }
     }
@@ -391,8 +391,10 @@ k_combine(DevMatrix M, DevState S) {
   double mnf = 0.0, mxf = 0.0;
   int32_t mni = 0, mxi = 0, ex = 0;
   float Tr = -f_inf(), Tl = -f_inf();
-  for (int32_t q = cb + lane; q < ce; q += kSliceW) {
-    Partial p = S.part[M.split_cidx[q]];
+  // each lane sums its pieces in order; the loads of four pieces are issued
+  // before they are consumed (a row split into hundreds of pieces would
+  // otherwise pay one dependent load latency per piece per lane)
+  auto add = [&](const Partial &p) {
     mnf += p.minfin;
     mxf += p.maxfin;
     mni += p.mininf;
@@ -400,7 +402,19 @@ k_combine(DevMatrix M, DevState S) {
     Tr = fmaxf(Tr, p.t.r1);
     Tl = fmaxf(Tl, p.t.l1);
     ex |= p.exact;
+  };
+  int32_t q = cb + lane;
+  for (; q + 3 * kSliceW < ce; q += 4 * kSliceW) {
+    int32_t ci[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ci[u] = M.split_cidx[q + u * kSliceW];
+    Partial p[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[u] = S.part[ci[u]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) add(p[u]);
   }
+  for (; q < ce; q += kSliceW) add(S.part[M.split_cidx[q]]);
   // butterfly reduction: a fixed pattern, so the sum is reproducible and
   // identical in every lane (binary64 addition is commutative)
 #pragma unroll
