@@ -379,6 +379,7 @@ k_round(DevMatrix M, DevState S) {
 // ------------------------------------------------------------ k_combine --
 
 constexpr int kCombineWarps = 8;
+constexpr int kCombineShort = 4;  // rows with at most this many pieces: one lane
 
 __global__ void __launch_bounds__(kCombineWarps * 32)
 k_combine(DevMatrix M, DevState S) {
@@ -391,9 +392,6 @@ k_combine(DevMatrix M, DevState S) {
   double mnf = 0.0, mxf = 0.0;
   int32_t mni = 0, mxi = 0, ex = 0;
   float Tr = -f_inf(), Tl = -f_inf();
-  // each lane sums its pieces in order; the loads of four pieces are issued
-  // before they are consumed (a row split into hundreds of pieces would
-  // otherwise pay one dependent load latency per piece per lane)
   auto add = [&](const Partial &p) {
     mnf += p.minfin;
     mxf += p.maxfin;
@@ -403,29 +401,44 @@ k_combine(DevMatrix M, DevState S) {
     Tl = fmaxf(Tl, p.t.l1);
     ex |= p.exact;
   };
-  int32_t q = cb + lane;
-  for (; q + 3 * kSliceW < ce; q += 4 * kSliceW) {
-    int32_t ci[4];
+  if (ce - cb <= kCombineShort) {
+    // most split rows have two or three pieces: one lane sums them in piece
+    // order (no cross-lane reduction, whose shuffles dominate otherwise)
+    if (lane != 0) return;
+    Partial p[kCombineShort];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) ci[u] = M.split_cidx[q + u * kSliceW];
-    Partial p[4];
+    for (int u = 0; u < kCombineShort; ++u)
+      if (cb + u < ce) p[u] = S.part[M.split_cidx[cb + u]];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) p[u] = S.part[ci[u]];
+    for (int u = 0; u < kCombineShort; ++u)
+      if (cb + u < ce) add(p[u]);
+  } else {
+    // each lane sums its pieces in order; the loads of four pieces are
+    // issued before they are consumed
+    int32_t q = cb + lane;
+    for (; q + 3 * kSliceW < ce; q += 4 * kSliceW) {
+      int32_t ci[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) add(p[u]);
-  }
-  for (; q < ce; q += kSliceW) add(S.part[M.split_cidx[q]]);
-  // butterfly reduction: a fixed pattern, so the sum is reproducible and
-  // identical in every lane (binary64 addition is commutative)
+      for (int u = 0; u < 4; ++u) ci[u] = M.split_cidx[q + u * kSliceW];
+      Partial p[4];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    mnf += __shfl_xor_sync(kFull, mnf, off);
-    mxf += __shfl_xor_sync(kFull, mxf, off);
-    mni += __shfl_xor_sync(kFull, mni, off);
-    mxi += __shfl_xor_sync(kFull, mxi, off);
-    Tr = fmaxf(Tr, __shfl_xor_sync(kFull, Tr, off));
-    Tl = fmaxf(Tl, __shfl_xor_sync(kFull, Tl, off));
-    ex |= __shfl_xor_sync(kFull, ex, off);
+      for (int u = 0; u < 4; ++u) p[u] = S.part[ci[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) add(p[u]);
+    }
+    for (; q < ce; q += kSliceW) add(S.part[M.split_cidx[q]]);
+    // butterfly reduction: a fixed pattern, so the sum is reproducible and
+    // identical in every lane (binary64 addition is commutative)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      mnf += __shfl_xor_sync(kFull, mnf, off);
+      mxf += __shfl_xor_sync(kFull, mxf, off);
+      mni += __shfl_xor_sync(kFull, mni, off);
+      mxi += __shfl_xor_sync(kFull, mxi, off);
+      Tr = fmaxf(Tr, __shfl_xor_sync(kFull, Tr, off));
+      Tl = fmaxf(Tl, __shfl_xor_sync(kFull, Tl, off));
+      ex |= __shfl_xor_sync(kFull, ex, off);
+    }
   }
   if (lane != 0) return;
   const int32_t row = M.split_row[w];
