@@ -75,11 +75,26 @@ __device__ __forceinline__ BParams load_params(const BCtrl *c) {
   return P;
 }
 
-// Bounds {L, U} of one (variable, node) entry; read-only within a kernel.
+// Bounds {L, U} of one (variable, node) entry and their screen widths;
+// read-only within a kernel.
 __device__ __forceinline__ double2 ld_bounds(const double2 *p) {
   double2 v;
   asm("ld.global.nc.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
   return v;
+}
+__device__ __forceinline__ float2 ld_widths(const float2 *p) {
+  float2 v;
+  asm("ld.global.nc.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+// Bounds and widths of one entry, as every kernel that changes them writes
+// them (the widths are those of the binary32 screen, see screen_widths).
+__device__ __forceinline__ void put_entry(const BatchState &S, int64_t e, double L, double U,
+                                          bool isint, float tau_dn, float eps_dn) {
+  float WU, WL;
+  screen_widths(L, U, isint, tau_dn, eps_dn, WU, WL);
+  S.cur[e] = make_double2(L, U);
+  S.wid[e] = make_float2(WU, WL);
 }
 
 __device__ __forceinline__ uint4 or4(uint4 a, uint4 b) {
@@ -154,9 +169,8 @@ struct BAct {
   float tr, tl;
 };
 
-__device__ __forceinline__ void act_add(double a, double2 b, uint8_t t, bool need_min,
-                                        bool need_max, bool screen, const BParams &P,
-                                        BAct &r) {
+__device__ __forceinline__ void act_add(double a, double2 b, float2 w, bool need_min,
+                                        bool need_max, bool screen, BAct &r) {
   const bool pos = d_pos(a);
   const double bmin = pos ? b.x : b.y;
   const double bmax = pos ? b.y : b.x;
@@ -171,11 +185,9 @@ __device__ __forceinline__ void act_add(double a, double2 b, uint8_t t, bool nee
     r.maxfin = fma(a, i ? 0.0 : bmax, r.maxfin);
   }
   if (screen) {
-    float WU, WL;
-    screen_widths(b.x, b.y, t != 0, P.tau_dn, P.eps_dn, WU, WL);
     const float au = absup_fast(a), ad = absdn_fast(a);
-    if (need_min) r.tr = fmaxf(r.tr, screen_prod(au, ad, pos ? WU : WL));
-    if (need_max) r.tl = fmaxf(r.tl, screen_prod(au, ad, pos ? WL : WU));
+    if (need_min) r.tr = fmaxf(r.tr, screen_prod(au, ad, pos ? w.x : w.y));
+    if (need_max) r.tl = fmaxf(r.tl, screen_prod(au, ad, pos ? w.y : w.x));
   }
 }
 
@@ -189,6 +201,7 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
   const double *vp = M.val + base;
   const int32_t *cp = M.col + base;
   const double2 *bp = S.cur + node;
+  const float2 *wp = S.wid + node;
   int k = 0;
   for (; k + 4 <= len; k += 4) {
     double a[4];
@@ -199,21 +212,21 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
       j[u] = __ldg(cp + (int64_t)(k + u) * kSliceW);
     }
     double2 b[4];
-    uint8_t t[4];
+    float2 w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       b[u] = ld_bounds(bp + (int64_t)j[u] * P.Bp);
-      t[u] = screen ? __ldg(S.vt + j[u]) : 0;
+      w[u] = screen ? ld_widths(wp + (int64_t)j[u] * P.Bp) : make_float2(0.0f, 0.0f);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) act_add(a[u], b[u], t[u], need_min, need_max, screen, P, r);
+    for (int u = 0; u < 4; ++u) act_add(a[u], b[u], w[u], need_min, need_max, screen, r);
   }
   for (; k < len; ++k) {
     const double a = __ldg(vp + (int64_t)k * kSliceW);
     const int32_t j = __ldg(cp + (int64_t)k * kSliceW);
     const double2 b = ld_bounds(bp + (int64_t)j * P.Bp);
-    const uint8_t t = screen ? __ldg(S.vt + j) : 0;
-    act_add(a, b, t, need_min, need_max, screen, P, r);
+    const float2 w = screen ? ld_widths(wp + (int64_t)j * P.Bp) : make_float2(0.0f, 0.0f);
+    act_add(a, b, w, need_min, need_max, screen, r);
   }
   if (!screen) r.tr = r.tl = f_inf();
   return r;
@@ -358,10 +371,10 @@ __device__ __forceinline__ void chunk_candidates(const DevMatrix &M, const Batch
     const int32_t j = __ldg(cp + (int64_t)k * kSliceW);
     unsigned sides = 0u;
     if (on) {
-      const double2 b = ld_bounds(S.cur + (int64_t)j * P.Bp + node);
-      float WU = f_inf(), WL = f_inf();
-      if (!rv.exact) screen_widths(b.x, b.y, __ldg(S.vt + j) != 0, P.tau_dn, P.eps_dn, WU, WL);
-      sides = nnz_sides(a, b.x, b.y, WU, WL, rv);
+      const int64_t e = (int64_t)j * P.Bp + node;
+      const double2 b = ld_bounds(S.cur + e);
+      const float2 w = ld_widths(S.wid + e);
+      sides = nnz_sides(a, b.x, b.y, w.x, w.y, rv);
     }
     const unsigned m = __ballot_sync(kFull, sides != 0u);
     if (m == 0u) continue;
@@ -687,7 +700,7 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
         const uint32_t j = e / (uint32_t)P.Bp, node = e % (uint32_t)P.Bp;
         const longlong2 kk = reinterpret_cast<const longlong2 *>(S.nkey)[e];
         const double L = val_of_key(kk.x), U = val_of_key(kk.y);
-        S.cur[e] = make_double2(L, U);
+        put_entry(S, e, L, U, S.vt[j] != 0, P.tau_dn, P.eps_dn);
         if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
           const bool cross = S.vt[j] ? (L > U) : (L > U + P.eps_feas * fmax(1.0, fabs(U)));
           if (cross) atomicOr(&s_inf[node >> 5], 1u << (node & 31));
@@ -780,11 +793,12 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
 // contradictory infinities set ctrl->err.  Padding nodes get [0, 0].
 __global__ void __launch_bounds__(kThreads)
 k_bprologue_bounds(BatchState S, int32_t n, int32_t count, int32_t Bp, const double *lb,
-                   const double *ub, const uint8_t *vartype, double eps_int, double eps_feas,
-                   double thr) {
+                   const double *ub, const uint8_t *vartype, double eps_int, double tau_rel,
+                   double eps_feas, double thr) {
   __shared__ double sL[32][33], sU[32][33];
   const double pinf = __longlong_as_double(0x7FF0000000000000ll);
   const long long k_thr = cmp_key(thr), k_mthr = cmp_key(-thr);
+  const float tau_dn = f32_dn(tau_rel), eps_dn = f32_dn(eps_int);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int G = Bp / 32;
   const int64_t tiles_x = ((int64_t)n + 31) / 32;
@@ -829,7 +843,7 @@ k_bprologue_bounds(BatchState S, int32_t n, int32_t count, int32_t Bp, const dou
       if (j < n) {
         const int64_t e = j * Bp + g * 32 + tx;
         const double L = sL[tx][yy], U = sU[tx][yy];
-        S.cur[e] = make_double2(L, U);
+        put_entry(S, e, L, U, vartype[j] != 0, tau_dn, eps_dn);
         reinterpret_cast<longlong2 *>(S.nkey)[e] = make_longlong2(key_of(L), key_of(U));
       }
     }
@@ -938,9 +952,10 @@ __global__ void k_bslot_reset(BatchState S, const int32_t *slots, int32_t count)
 // into the slot's node column.  A crossing input flags the node.
 __global__ void __launch_bounds__(kThreads)
 k_bslot_fill(BatchState S, const int32_t *slots, int32_t count, const double *stage, int32_t n,
-             int32_t Bp, double eps_int, double eps_feas, double thr) {
+             int32_t Bp, double eps_int, double tau_rel, double eps_feas, double thr) {
   const double pinf = __longlong_as_double(0x7FF0000000000000ll);
   const long long k_thr = cmp_key(thr), k_mthr = cmp_key(-thr);
+  const float tau_dn = f32_dn(tau_rel), eps_dn = f32_dn(eps_int);
   const int64_t total = (int64_t)count * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -957,7 +972,7 @@ k_bslot_fill(BatchState S, const int32_t *slots, int32_t count, const double *st
     if (cmp_key(L) > cmp_key(U) && (isint || L > U + eps_feas * fmax(1.0, fabs(U))))
       atomicOr(&S.inf_bits[node >> 5], 1u << (node & 31));
     const int64_t e = j * Bp + node;
-    S.cur[e] = make_double2(L, U);
+    put_entry(S, e, L, U, isint, tau_dn, eps_dn);
     reinterpret_cast<longlong2 *>(S.nkey)[e] = make_longlong2(key_of(L), key_of(U));
   }
 }
@@ -1022,7 +1037,8 @@ int grid_for(int64_t work, int threads, int max_blocks) {
 cudaError_t launch_batch_prologue(const DevMatrix &M, const BatchState &S, int32_t count,
                                   const double *lb, const double *ub, const uint8_t *vartype,
                                   const double *lhs, const double *rhs, double eps_int,
-                                  double eps_feas, double thr, int num_sms, cudaStream_t st) {
+                                  double tau_rel, double eps_feas, double thr, int num_sms,
+                                  cudaStream_t st) {
   const int32_t Bp = (count + 31) / 32 * 32;
   const int64_t tiles = (((int64_t)M.n + 31) / 32) * (Bp / 32);
   int64_t total = M.n > M.m ? M.n : M.m;
@@ -1034,7 +1050,7 @@ cudaError_t launch_batch_prologue(const DevMatrix &M, const BatchState &S, int32
   if (e != cudaSuccess || M.n == 0) return e;
   int nb = (int)(tiles < (int64_t)num_sms * 16 ? tiles : (int64_t)num_sms * 16);
   k_bprologue_bounds<<<nb, kThreads, 0, st>>>(S, M.n, count, Bp, lb, ub, vartype, eps_int,
-                                              eps_feas, thr);
+                                              tau_rel, eps_feas, thr);
   return cudaGetLastError();
 }
 
@@ -1099,14 +1115,14 @@ cudaError_t launch_slots_init(const DevMatrix &M, const BatchState &S, int32_t B
 
 cudaError_t launch_slots_admit(const DevMatrix &M, const BatchState &S, int32_t Bp,
                                const int32_t *slots, int32_t count, const double *stage,
-                               double eps_int, double eps_feas, double thr, int num_sms,
-                               cudaStream_t st) {
+                               double eps_int, double tau_rel, double eps_feas, double thr,
+                               int num_sms, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   k_bslot_reset<<<(count + 127) / 128, 128, 0, st>>>(S, slots, count);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || M.n == 0) return e;
   k_bslot_fill<<<grid_for((int64_t)count * M.n, kThreads, num_sms * 8), kThreads, 0, st>>>(
-      S, slots, count, stage, M.n, Bp, eps_int, eps_feas, thr);
+      S, slots, count, stage, M.n, Bp, eps_int, tau_rel, eps_feas, thr);
   return cudaGetLastError();
 }
 

@@ -498,6 +498,7 @@ int batch_state(const DevMatrix &M, int32_t Bp, std::vector<void *> &allocs, Bat
 #define ATRY(x) \
   if ((rc = (x)) != DP_OK) return rc
   ATRY(track_alloc(allocs, &S.cur, n * Bp, bytes));
+  ATRY(track_alloc(allocs, &S.wid, n * Bp, bytes));
   ATRY(track_alloc(allocs, &S.nkey, 2 * n * Bp, bytes));
   ATRY(track_alloc(allocs, &S.chg[0], n * Gs, bytes));
   ATRY(track_alloc(allocs, &S.chg[1], n * Gs, bytes));
@@ -738,7 +739,8 @@ int nodes_call(dp_ctx *ctx, const dp_matrix *cmat, int32_t count, const double *
       CUDA_TRY(cudaMemsetAsync(b->S.chg[1], 0, sizeof(uint32_t) * Gs * n, st));
     }
     CUDA_TRY(dp::launch_batch_prologue(mat->M, b->S, cnt, d_lb, d_ub, d_vt, d_lhs, d_rhs,
-                                       p.eps_int, p.eps_feas, p.inf_threshold, ctx->num_sms, st));
+                                       p.eps_int, p.tau_rel, p.eps_feas, p.inf_threshold,
+                                       ctx->num_sms, st));
     if (p.max_rounds > 0 && !hostloop) CUDA_TRY(cudaGraphLaunch(b->exec, st));
     if (p.max_rounds > 0 && hostloop) {
       int r2 = batch_hostloop(mat, b, p.max_rounds, kernel_ms, kernel_launches);

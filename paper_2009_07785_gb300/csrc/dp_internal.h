@@ -158,6 +158,7 @@ struct BCtrl {
 
 struct BatchState {
   double2 *cur;         // [n*Bp] {L, U} at the start of the round
+  float2 *wid;          // [n*Bp] screen widths {W_U, W_L} of those bounds
   long long *nkey;      // [2*n*Bp] next state as order-preserving keys
   uint32_t *chg[2];     // [n*G] nodes of each group whose bounds of var j changed
   uint32_t *dirty[2];   // [2*n*Bp] entries e = j*Bp+node improved in a round

@@ -35,7 +35,8 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S,
 cudaError_t launch_batch_prologue(const DevMatrix &M, const BatchState &S, int32_t count,
                                   const double *lb, const double *ub, const uint8_t *vartype,
                                   const double *lhs, const double *rhs, double eps_int,
-                                  double eps_feas, double thr, int num_sms, cudaStream_t st);
+                                  double tau_rel, double eps_feas, double thr, int num_sms,
+                                  cudaStream_t st);
 cudaError_t launch_batch_epilogue(const DevMatrix &M, const BatchState &S, int32_t count,
                                   double *lb_out, double *ub_out, int num_sms,
                                   cudaStream_t st);
@@ -58,8 +59,8 @@ cudaError_t launch_slots_init(const DevMatrix &M, const BatchState &S, int32_t B
                               double thr, int num_sms, cudaStream_t st);
 cudaError_t launch_slots_admit(const DevMatrix &M, const BatchState &S, int32_t Bp,
                                const int32_t *slots, int32_t count, const double *stage,
-                               double eps_int, double eps_feas, double thr, int num_sms,
-                               cudaStream_t st);
+                               double eps_int, double tau_rel, double eps_feas, double thr,
+                               int num_sms, cudaStream_t st);
 cudaError_t launch_slots_extract(const DevMatrix &M, const BatchState &S, int32_t Bp,
                                  const int32_t *slots, int32_t count, double *out,
                                  int num_sms, cudaStream_t st);

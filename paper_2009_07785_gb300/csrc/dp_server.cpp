@@ -390,8 +390,9 @@ bool service(dp_server *s, Lane &L) {
                           cudaMemcpyHostToDevice, L.stream);
     if (e == cudaSuccess)
       e = dp::launch_slots_admit(L.mat->M, L.S, Bp, L.d_admit, cnt, L.d_in,
-                                 s->cfg.params.eps_int, s->cfg.params.eps_feas,
-                                 s->cfg.params.inf_threshold, s->ctx->num_sms, L.stream);
+                                 s->cfg.params.eps_int, s->cfg.params.tau_rel,
+                                 s->cfg.params.eps_feas, s->cfg.params.inf_threshold,
+                                 s->ctx->num_sms, L.stream);
     if (e != cudaSuccess) s->error = DP_ERR_CUDA;
     std::lock_guard<std::mutex> g(s->mu);
     s->stats.admissions += cnt;
