@@ -134,6 +134,33 @@ int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                          const double *val, int32_t chunk, const double *lhs,
                          const double *rhs, dp_matrix **out);
 
+/*
+ * Loads `count` independent problems as one matrix: problem k has m[k]
+ * rows, n[k] variables and the CSR arrays row_ptr[k], col_idx[k], val[k]
+ * (host, as in dp_matrix_load, columns local to the problem); lhs/rhs
+ * (arrays of count host pointers, or both NULL) are the optional side hints
+ * of dp_matrix_load_sides.  The result is their block-diagonal union: rows
+ * and variables are concatenated in problem order (dp_matrix_set_offsets
+ * gives each problem's first row and variable), and it is propagated with
+ * dp_propagate_set, which stops and counts rounds per problem -- many
+ * matrices of uneven size in one device-side round loop, every problem
+ * reaching exactly its own dp_propagate result.  The paper propagates one
+ * problem per call; this is the batched-matrices form.
+ * Returns DP_OK, DP_ERR_INVALID_ARG, DP_ERR_BAD_CSR, DP_ERR_OOM or
+ * DP_ERR_CUDA.
+ */
+int dp_matrix_load_set(dp_ctx *ctx, int32_t count, const int32_t *m,
+                       const int32_t *n, const int64_t *const *row_ptr,
+                       const int32_t *const *col_idx, const double *const *val,
+                       int32_t chunk, const double *const *lhs,
+                       const double *const *rhs, dp_matrix **out);
+
+/* Problems of a set: *count, and (if not NULL) row_off[count+1] and
+ * var_off[count+1], the first row and variable of each problem in the
+ * union (the last entries are the totals).  For a plain matrix *count = 0. */
+int dp_matrix_set_offsets(const dp_matrix *set, int32_t *count,
+                          int32_t *row_off, int32_t *var_off);
+
 /* Frees a matrix; NULL is a no-op. */
 void dp_matrix_free(dp_matrix *mat);
 
@@ -166,6 +193,24 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
                  const double *ub, const uint8_t *vartype, const double *lhs,
                  const double *rhs, const dp_params *params, double *lb_out,
                  double *ub_out, int32_t *infeasible, int32_t *rounds);
+
+/*
+ * Propagates every problem of a set (dp_matrix_load_set) in one device-side
+ * round loop.  lb, ub, vartype (length: total variables) and lhs, rhs
+ * (total rows) are the problems' arrays concatenated in problem order
+ * (host or device); lb_out/ub_out likewise.  Each problem stops on its own
+ * (no change, infeasibility, or the cap) and keeps its bounds from then on:
+ * its results equal dp_propagate on that problem alone.  infeasible[count],
+ * rounds[count] and status[count] (HOST int32; status may be NULL: 1 = the
+ * cap stopped it with a change in its last round) are per problem.
+ * Returns DP_OK, DP_CAP_HIT (some problem hit the cap), or an error as
+ * dp_propagate (DP_ERR_INVALID_ARG for a matrix that is not a set).
+ */
+int dp_propagate_set(dp_ctx *ctx, const dp_matrix *set, const double *lb,
+                     const double *ub, const uint8_t *vartype,
+                     const double *lhs, const double *rhs,
+                     const dp_params *params, double *lb_out, double *ub_out,
+                     int32_t *infeasible, int32_t *rounds, int32_t *status);
 
 /*
  * The same propagation with the round loop driven from the host: after each

@@ -30,8 +30,8 @@ DP_ERR_TIMEOUT = -6
 
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
-           "dp_matrix_load_sides", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
-           "dp_propagate_noalloc", "dp_propagate_nodes",
+           "dp_matrix_load_sides", "dp_matrix_load_set", "dp_matrix_set_offsets", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
+           "dp_propagate_noalloc", "dp_propagate_nodes", "dp_propagate_set",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
            "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
            "dp_server_destroy")
@@ -84,6 +84,13 @@ def lib() -> C.CDLL:
     L.dp_matrix_load.restype = C.c_int
     L.dp_matrix_load_sides.argtypes = [vp, i32, i32, i64, vp, vp, vp, i32, vp, vp, C.POINTER(vp)]
     L.dp_matrix_load_sides.restype = C.c_int
+    L.dp_matrix_load_set.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, C.POINTER(vp)]
+    L.dp_matrix_load_set.restype = C.c_int
+    L.dp_matrix_set_offsets.argtypes = [vp, C.POINTER(i32), vp, vp]
+    L.dp_matrix_set_offsets.restype = C.c_int
+    L.dp_propagate_set.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp, vp,
+                                   vp, vp]
+    L.dp_propagate_set.restype = C.c_int
     L.dp_matrix_free.argtypes = [vp]
     L.dp_matrix_free.restype = None
     L.dp_matrix_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
@@ -240,6 +247,87 @@ class Matrix:
 
     def __exit__(self, *a):
         self.close()
+
+
+class MatrixSet(Matrix):
+    """A dp_matrix holding several independent problems (dp_matrix_load_set):
+    their block-diagonal union, propagated per problem by dp_propagate_set.
+    row_off / var_off give each problem's first row and variable."""
+
+    def __init__(self, ctx: Context, problems, chunk: int = 0, sides: bool = False):
+        """problems: sequence of (m, n, row_ptr, col_idx, val) or objects with
+        those attributes (and lhs, rhs when sides=True)."""
+        ps = [p if isinstance(p, tuple) else (p.m, p.n, p.row_ptr, p.col, p.val)
+              for p in problems]
+        k = len(ps)
+        rp = [np.ascontiguousarray(p[2], dtype=np.int64) for p in ps]
+        ci = [np.ascontiguousarray(p[3], dtype=np.int32) for p in ps]
+        va = [np.ascontiguousarray(p[4], dtype=np.float64) for p in ps]
+        m = np.asarray([p[0] for p in ps], dtype=np.int32)
+        n = np.asarray([p[1] for p in ps], dtype=np.int32)
+        P64, P32, PD = C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double)
+        rpa = (P64 * k)(*[a.ctypes.data_as(P64) for a in rp])
+        cia = (P32 * k)(*[a.ctypes.data_as(P32) for a in ci])
+        vaa = (PD * k)(*[a.ctypes.data_as(PD) for a in va])
+        lh = rh = None
+        keep = []
+        if sides:
+            ls = [np.ascontiguousarray(p.lhs, dtype=np.float64) for p in problems]
+            rs = [np.ascontiguousarray(p.rhs, dtype=np.float64) for p in problems]
+            keep = ls + rs
+            lh = (PD * k)(*[a.ctypes.data_as(PD) for a in ls])
+            rh = (PD * k)(*[a.ctypes.data_as(PD) for a in rs])
+        h = C.c_void_p()
+        _check(lib().dp_matrix_load_set(ctx.handle, k, m.ctypes.data, n.ctypes.data, rpa, cia, vaa,
+                                        int(chunk), lh, rh, C.byref(h)), "dp_matrix_load_set")
+        del keep
+        self.handle = h
+        self.ctx = ctx
+        self.m, self.n = int(m.sum()), int(n.sum())
+        self.count = k
+        cnt = C.c_int32()
+        self.row_off = np.zeros(k + 1, dtype=np.int32)
+        self.var_off = np.zeros(k + 1, dtype=np.int32)
+        _check(lib().dp_matrix_set_offsets(h, C.byref(cnt), self.row_off.ctypes.data,
+                                           self.var_off.ctypes.data), "dp_matrix_set_offsets")
+
+
+def dp_matrix_load_set(ctx: Context, problems, chunk: int = 0, sides: bool = False) -> MatrixSet:
+    return MatrixSet(ctx, problems, chunk, sides)
+
+
+def dp_matrix_set_offsets(mset: MatrixSet) -> tuple:
+    return mset.row_off, mset.var_off
+
+
+@dataclass
+class SetResult:
+    lb: object
+    ub: object
+    infeasible: np.ndarray
+    rounds: np.ndarray
+    cap_hit: np.ndarray
+    status: int
+
+
+def dp_propagate_set(ctx: Context, mset: MatrixSet, lb, ub, vartype, lhs, rhs,
+                     params: dp_params | None = None, lb_out=None, ub_out=None) -> SetResult:
+    """Propagates every problem of a set; arrays are the problems' arrays
+    concatenated in problem order.  Per-problem flags and round counts."""
+    if lb_out is None:
+        lb_out = _like(lb, mset.n)
+    if ub_out is None:
+        ub_out = _like(lb, mset.n)
+    k = max(getattr(mset, "count", 0), 1)  # a plain matrix is rejected by the library
+    inf = np.zeros(k, dtype=np.int32)
+    rounds = np.zeros(k, dtype=np.int32)
+    cap = np.zeros(k, dtype=np.int32)
+    rc = _check(lib().dp_propagate_set(ctx.handle, mset.handle, _ptr(lb), _ptr(ub), _ptr(vartype),
+                                       _ptr(lhs), _ptr(rhs),
+                                       C.byref(params) if params is not None else None,
+                                       _ptr(lb_out), _ptr(ub_out), inf.ctypes.data,
+                                       rounds.ctypes.data, cap.ctypes.data), "dp_propagate_set")
+    return SetResult(lb_out, ub_out, inf, rounds, cap, rc)
 
 
 def dp_matrix_load(ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int = 0) -> Matrix:

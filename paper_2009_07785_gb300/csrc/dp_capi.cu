@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -203,6 +204,7 @@ void dp_matrix_free(dp_matrix *mat) {
   cudaSetDevice(mat->ctx->device);
   cudaStreamSynchronize(mat->ctx->stream);
   free_batch(mat->batch);
+  if (mat->h_inst) cudaFreeHost(mat->h_inst);
   if (mat->exec) cudaGraphExecDestroy(mat->exec);
   if (mat->graph) cudaGraphDestroy(mat->graph);
   for (void *p : mat->allocs) cudaFree(p);
@@ -217,10 +219,16 @@ int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                               out);
 }
 
-int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
-                         const int64_t *row_ptr, const int32_t *col_idx, const double *val,
-                         int32_t chunk, const double *lhs, const double *rhs,
-                         dp_matrix **out) {
+}  // extern "C"
+
+namespace {
+
+// Loads a matrix; with row_off/var_off (count+1 offsets each) it is the
+// block-diagonal union of `count` independent problems.
+int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+              const int32_t *col_idx, const double *val, int32_t chunk, const double *lhs,
+              const double *rhs, const std::vector<int32_t> *row_off,
+              const std::vector<int32_t> *var_off, dp_matrix **out) {
   if (!ctx || !out) return DP_ERR_INVALID_ARG;
   *out = nullptr;
   if ((lhs == nullptr) != (rhs == nullptr)) return DP_ERR_INVALID_ARG;
@@ -280,6 +288,35 @@ int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
   TRY(dev_alloc(mat, &mat->st_rhs, (size_t)m));
   TRY(dev_alloc(mat, &mat->out_lb, (size_t)n));
   TRY(dev_alloc(mat, &mat->out_ub, (size_t)n));
+  if (row_off) {
+    // problem of every chunk slot (by its row) and of every variable
+    const int32_t count = (int32_t)row_off->size() - 1;
+    std::vector<int32_t> slot_inst(H.chunk_row.size(), -1), var_inst((size_t)n, 0);
+    for (size_t c = 0; c < H.chunk_row.size(); ++c) {
+      const int32_t r = H.chunk_row[c];
+      if (r >= 0)
+        slot_inst[c] = (int32_t)(std::upper_bound(row_off->begin(), row_off->end(), r) -
+                                 row_off->begin()) - 1;
+    }
+    for (int32_t k = 0; k < count; ++k)
+      for (int32_t j = (*var_off)[k]; j < (*var_off)[k + 1]; ++j) var_inst[(size_t)j] = k;
+    TRY(upload(mat, slot_inst, &S.I.slot_inst, st));
+    TRY(upload(mat, var_inst, &S.I.var_inst, st));
+    TRY(dev_alloc(mat, &S.I.changed, (size_t)count));
+    TRY(dev_alloc(mat, &S.I.infeasible, (size_t)count));
+    TRY(dev_alloc(mat, &S.I.done, (size_t)count));
+    TRY(dev_alloc(mat, &S.I.rounds, (size_t)count));
+    TRY(dev_alloc(mat, &S.I.status, (size_t)count));
+    S.I.ninst = count;
+    mat->ninst = count;
+    mat->row_off = *row_off;
+    mat->var_off = *var_off;
+    if (cudaMallocHost(&mat->h_inst, sizeof(int32_t) * 3 * (size_t)count) != cudaSuccess) {
+      cudaGetLastError();
+      dp_matrix_free(mat);
+      return DP_ERR_OOM;
+    }
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     dp_matrix_free(mat);
@@ -288,6 +325,84 @@ int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
   TRY(build_graph(mat));
 #undef TRY
   *out = mat;
+  return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col_idx, const double *val,
+                         int32_t chunk, const double *lhs, const double *rhs,
+                         dp_matrix **out) {
+  return load_impl(ctx, m, n, nnz, row_ptr, col_idx, val, chunk, lhs, rhs, nullptr, nullptr,
+                   out);
+}
+
+int dp_matrix_load_set(dp_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
+                       const int64_t *const *row_ptr, const int32_t *const *col_idx,
+                       const double *const *val, int32_t chunk, const double *const *lhs,
+                       const double *const *rhs, dp_matrix **out) {
+  if (!ctx || !out || count <= 0 || !m || !n || !row_ptr || !col_idx || !val)
+    return DP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((lhs == nullptr) != (rhs == nullptr)) return DP_ERR_INVALID_ARG;
+  std::vector<int32_t> row_off(1, 0), var_off(1, 0);
+  int64_t mt = 0, nt = 0, nzt = 0;
+  for (int32_t k = 0; k < count; ++k) {
+    if (m[k] < 0 || n[k] < 0 || (m[k] > 0 && !row_ptr[k])) return DP_ERR_INVALID_ARG;
+    mt += m[k];
+    nt += n[k];
+    if (m[k] > 0) nzt += row_ptr[k][m[k]];
+    if (mt >= (int64_t(1) << 31) || nt >= (int64_t(1) << 31) || nzt >= (int64_t(1) << 31))
+      return DP_ERR_INVALID_ARG;
+    row_off.push_back((int32_t)mt);
+    var_off.push_back((int32_t)nt);
+  }
+  std::vector<int64_t> rp;
+  std::vector<int32_t> col;
+  std::vector<double> vv, sl, sr;
+  try {
+    rp.reserve((size_t)mt + 1);
+    col.reserve((size_t)nzt);
+    vv.reserve((size_t)nzt);
+    rp.push_back(0);
+    for (int32_t k = 0; k < count; ++k) {
+      const int64_t base = rp.back();
+      for (int32_t i = 0; i < m[k]; ++i) rp.push_back(base + row_ptr[k][i + 1]);
+      const int64_t nz = m[k] > 0 ? row_ptr[k][m[k]] : 0;
+      if (m[k] > 0 && row_ptr[k][0] != 0) return DP_ERR_BAD_CSR;
+      if (nz > 0 && (!col_idx[k] || !val[k])) return DP_ERR_INVALID_ARG;
+      for (int64_t q = 0; q < nz; ++q) {
+        const int32_t c = col_idx[k][q];
+        if (c < 0 || c >= n[k]) return DP_ERR_BAD_CSR;
+        col.push_back(c + var_off[(size_t)k]);
+        vv.push_back(val[k][q]);
+      }
+      if (lhs) {
+        for (int32_t i = 0; i < m[k]; ++i) {
+          sl.push_back(lhs[k][i]);
+          sr.push_back(rhs[k][i]);
+        }
+      }
+    }
+  } catch (const std::bad_alloc &) {
+    return DP_ERR_OOM;
+  }
+  return load_impl(ctx, (int32_t)mt, (int32_t)nt, nzt, rp.data(), col.data(), vv.data(), chunk,
+                   lhs ? sl.data() : nullptr, lhs ? sr.data() : nullptr, &row_off, &var_off,
+                   out);
+}
+
+int dp_matrix_set_offsets(const dp_matrix *set, int32_t *count, int32_t *row_off,
+                          int32_t *var_off) {
+  if (!set) return DP_ERR_INVALID_ARG;
+  if (count) *count = set->ninst;
+  for (int32_t k = 0; k <= set->ninst && set->ninst > 0; ++k) {
+    if (row_off) row_off[k] = set->row_off[(size_t)k];
+    if (var_off) var_off[k] = set->var_off[(size_t)k];
+  }
   return DP_OK;
 }
 
@@ -396,6 +511,44 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
   if (rc) return rc;
   if (p.max_rounds > 0) CUDA_TRY(cudaGraphLaunch(mat->exec, ctx->stream));
   return end_call(ctx, mat, p, lb_out, ub_out, infeasible, rounds);
+}
+
+int dp_propagate_set(dp_ctx *ctx, const dp_matrix *cset, const double *lb, const double *ub,
+                     const uint8_t *vartype, const double *lhs, const double *rhs,
+                     const dp_params *params, double *lb_out, double *ub_out,
+                     int32_t *infeasible, int32_t *rounds, int32_t *status) {
+  if (!cset || cset->ninst <= 0 || !infeasible || !rounds) return DP_ERR_INVALID_ARG;
+  dp_params p;
+  int32_t dummy_inf = 0, dummy_rounds = 0;
+  int rc = check_call(ctx, cset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, &dummy_inf,
+                      &dummy_rounds, &p);
+  if (rc) return rc;
+  dp_matrix *set = const_cast<dp_matrix *>(cset);
+  rc = begin_call(ctx, set, lb, ub, vartype, lhs, rhs, p);
+  if (rc) return rc;
+  cudaStream_t st = ctx->stream;
+  const dp::InstState &I = set->S.I;
+  const size_t cb = sizeof(int32_t) * (size_t)I.ninst;
+  CUDA_TRY(cudaMemsetAsync(I.changed, 0, cb, st));
+  CUDA_TRY(cudaMemsetAsync(I.infeasible, 0, cb, st));
+  CUDA_TRY(cudaMemsetAsync(I.done, 0, cb, st));
+  CUDA_TRY(cudaMemsetAsync(I.rounds, 0, cb, st));
+  CUDA_TRY(cudaMemsetAsync(I.status, 0, cb, st));
+  if (p.max_rounds > 0) CUDA_TRY(cudaGraphLaunch(set->exec, st));
+  int32_t *h = set->h_inst;
+  CUDA_TRY(cudaMemcpyAsync(h, I.infeasible, cb, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(h + I.ninst, I.rounds, cb, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(h + 2 * I.ninst, I.status, cb, cudaMemcpyDeviceToHost, st));
+  rc = end_call(ctx, set, p, lb_out, ub_out, &dummy_inf, &dummy_rounds);
+  if (rc < 0) return rc;
+  bool cap = false;
+  for (int32_t k = 0; k < I.ninst; ++k) {
+    infeasible[k] = h[k] ? 1 : 0;
+    rounds[k] = h[I.ninst + k];
+    if (status) status[k] = h[2 * I.ninst + k];
+    cap |= h[2 * I.ninst + k] != 0;
+  }
+  return cap ? DP_CAP_HIT : DP_OK;
 }
 
 int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
@@ -576,6 +729,7 @@ int ensure_batch(dp_matrix *mat, int32_t Bp) {
   if (mat->batch) {
     cudaStreamSynchronize(mat->ctx->stream);
     free_batch(mat->batch);
+  if (mat->h_inst) cudaFreeHost(mat->h_inst);
     mat->batch = nullptr;
   }
   BatchWs *b = new (std::nothrow) BatchWs();

@@ -106,6 +106,21 @@ struct DevMatrix {
   const int32_t *split_cidx;// chunk slots of the split rows' pieces, row by row
 };
 
+// Several independent problems in one matrix (their block-diagonal union:
+// each problem owns its rows and variables) with per-problem termination.
+// All pointers are null for a single problem.
+struct InstState {
+  const int32_t *slot_inst;  // [chunk slots] problem of each chunk's row
+  const int32_t *var_inst;   // [n] problem of each variable
+  int32_t *changed;          // [ninst] a candidate was accepted this round
+  int32_t *infeasible;       // [ninst]
+  int32_t *done;             // [ninst] stopped: no change, infeasible or the cap
+  int32_t *rounds;           // [ninst] executed rounds
+  int32_t *status;           // [ninst] 1 = stopped by the cap
+  int32_t ninst;
+  int32_t pad;
+};
+
 struct DevState {
   CandEntry *queue;     // [padded slots] candidate queue
   RowSum *rowsum;       // [chunk slots] sums of rows with queued nonzeros
@@ -116,6 +131,7 @@ struct DevState {
   Partial *part;        // [nslices_split*32]
   RowTot *rowtot;       // [nsplit_rows]
   Ctrl *ctrl;
+  InstState I;          // problem sets only
 };
 
 // ------------------------------------------------------ batched B&B nodes --

@@ -211,6 +211,7 @@ __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t,
 // ---------------------------------------------------------- k_cand_queue --
 
 // Evaluates the queued nonzeros, one per thread (grid-stride).
+template <bool kMulti>
 __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
@@ -237,7 +238,8 @@ __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
     rv.thr_r = rv.thr_l = f_inf();
     rv.exact = 0;
     rv.act = 1;
-    nnz_candidates(a, j, L, U, fl, E.cs & 3u, rv, prm, S.keys, &S.ctrl->changed);
+    int32_t *changed = kMulti ? &S.I.changed[S.I.slot_inst[c]] : &S.ctrl->changed;
+    nnz_candidates(a, j, L, U, fl, E.cs & 3u, rv, prm, S.keys, changed);
   }
 }
 
@@ -247,6 +249,7 @@ constexpr int kRoundWarps = 8;
 constexpr int kGroup = 4;         // slots per group in the activity loop
 constexpr int kRoundMinBlocks = 3;  // resident blocks per SM the register budget allows
 
+template <bool kMulti>
 __global__ void __launch_bounds__(kRoundWarps * 32, kRoundMinBlocks)
 k_round(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
@@ -257,8 +260,18 @@ k_round(DevMatrix M, DevState S) {
   if (slice >= M.nslices) return;  // warp-uniform
   const int64_t c = (int64_t)slice * kSliceW + lane;
   const int32_t lenf = M.chunk_len[c];
-  const int32_t len = lenf & kLenMask;
-  const int32_t row = M.chunk_row[c];
+  int32_t len = lenf & kLenMask;
+  int32_t row = M.chunk_row[c];
+  int32_t *inf_flag = &S.ctrl->infeasible;
+  if (kMulti && row >= 0) {  // a stopped problem's rows do nothing
+    const int32_t inst = S.I.slot_inst[c];
+    if (S.I.done[inst]) {
+      row = -1;
+      len = 0;
+    } else {
+      inf_flag = &S.I.infeasible[inst];
+    }
+  }
   const int64_t sbase = M.slice_off[slice];
   const double *svp = M.val + sbase;
   const int32_t *scp = M.col + sbase;
@@ -369,7 +382,7 @@ k_round(DevMatrix M, DevState S) {
   if (row >= 0) {
     rv.lhs = sd.x;
     rv.rhs = sd.y;
-    row_sides(rv, t.r1, t.l1, ctrl->eps_feas, &S.ctrl->infeasible);
+    row_sides(rv, t.r1, t.l1, ctrl->eps_feas, inf_flag);
   } else {
     rv.lhs = rv.rhs = 0.0;
   }
@@ -381,6 +394,7 @@ k_round(DevMatrix M, DevState S) {
 constexpr int kCombineWarps = 8;
 constexpr int kCombineShort = 4;  // rows with at most this many pieces: one lane
 
+template <bool kMulti>
 __global__ void __launch_bounds__(kCombineWarps * 32)
 k_combine(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
@@ -389,6 +403,15 @@ k_combine(DevMatrix M, DevState S) {
   const int lane = threadIdx.x & 31;
   if (w >= M.nsplit_rows) return;
   const int32_t cb = M.split_cbeg[w], ce = M.split_cbeg[w + 1];
+  int32_t *inf_flag = &S.ctrl->infeasible;
+  if (kMulti) {
+    const int32_t inst = S.I.slot_inst[M.split_cidx[cb]];
+    if (S.I.done[inst]) {  // a stopped problem: no candidates
+      if (lane == 0) S.rowtot[w].active = 0;
+      return;
+    }
+    inf_flag = &S.I.infeasible[inst];
+  }
   double mnf = 0.0, mxf = 0.0;
   int32_t mni = 0, mxi = 0, ex = 0;
   float Tr = -f_inf(), Tl = -f_inf();
@@ -451,7 +474,7 @@ k_combine(DevMatrix M, DevState S) {
   rv.rhs = S.rhs[row];
   rv.exact = ex;
   if (ex) Tr = Tl = f_inf();
-  row_sides(rv, Tr, Tl, ctrl->eps_feas, &S.ctrl->infeasible);
+  row_sides(rv, Tr, Tl, ctrl->eps_feas, inf_flag);
   RowTot rt;
   rt.minfin = mnf;
   rt.maxfin = mxf;
@@ -516,6 +539,7 @@ constexpr int kFinishThreads = 256;
 // Ends a round: the next state becomes the current one.  The last block to
 // arrive (threadfence-reduction pattern; nobody waits) counts the round and
 // sets the WHILE condition of the enclosing graph node.
+template <bool kMulti>
 __global__ void __launch_bounds__(kFinishThreads)
 k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHandle handle,
          int use_cond) {
@@ -526,35 +550,71 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHand
   if (!err) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
+      int32_t *inf_flag = &ctrl->infeasible;
+      if (kMulti) {
+        const int32_t inst = S.I.var_inst[j];
+        if (S.I.done[inst]) continue;  // a stopped problem keeps its bounds
+        inf_flag = &S.I.infeasible[inst];
+      }
       longlong2 kk = reinterpret_cast<const longlong2 *>(S.keys)[j];
       double L = val_of_key(kk.x), U = val_of_key(kk.y);
       uint32_t vt = vartype[j] ? 1u : 0u;
       if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
         bool cross = vt ? (L > U) : (L > U + eps_feas * fmax(1.0, fabs(U)));
-        if (cross) set_flag(&ctrl->infeasible);
+        if (cross) set_flag(inf_flag);
       }
       write_var(S.rec + j, L, U, vt, tau_dn, eps_dn);
     }
   }
+  __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
-    if (prev == gridDim.x - 1) {
-      __threadfence();
-      volatile Ctrl *vc = ctrl;
-      int32_t r = vc->round + 1;
-      vc->round = r;
-      int32_t ch = vc->changed;
-      int32_t cont = (ch && !vc->infeasible && !vc->err && r < vc->max_rounds) ? 1 : 0;
-      vc->last_changed = ch;
-      vc->changed = 0;
-      vc->qcount = 0;
-      vc->blocks_done = 0;
-      __threadfence();
-      if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
-    }
+    s_last = prev == gridDim.x - 1;
   }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  volatile Ctrl *vc = ctrl;
+  const int32_t r = vc->round + 1;
+  int32_t cont;
+  if (kMulti) {
+    // each problem counts its rounds and stops on its own (no change,
+    // infeasible, or the cap); the loop runs while any problem is live
+    volatile int32_t *ch = S.I.changed, *inf = S.I.infeasible, *dn = S.I.done;
+    int live = 0;
+    for (int i = threadIdx.x; i < S.I.ninst; i += blockDim.x) {
+      if (dn[i]) continue;
+      const int32_t ri = S.I.rounds[i] + 1;
+      S.I.rounds[i] = ri;
+      int32_t d = 0;
+      if (inf[i]) d = 1;
+      else if (!ch[i]) d = 1;
+      else if (ri >= vc->max_rounds) {
+        d = 1;
+        S.I.status[i] = 1;
+      }
+      dn[i] = d;
+      ch[i] = 0;
+      live |= !d;
+    }
+    live = __syncthreads_or(live);
+    cont = (live && !vc->err && r < vc->max_rounds) ? 1 : 0;
+    if (threadIdx.x != 0) return;
+    vc->last_changed = live;
+  } else {
+    if (threadIdx.x != 0) return;
+    int32_t chg = vc->changed;
+    cont = (chg && !vc->infeasible && !vc->err && r < vc->max_rounds) ? 1 : 0;
+    vc->last_changed = chg;
+  }
+  vc->round = r;
+  vc->changed = 0;
+  vc->qcount = 0;
+  vc->blocks_done = 0;
+  __threadfence();
+  if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
 }
 
 // ------------------------------------------------------ prologue/epilogue --
@@ -668,23 +728,21 @@ cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out, double
   return cudaGetLastError();
 }
 
-// Launches one round's kernels on `st`.  In the graph body (use_cond = 1)
-// k_finish sets the WHILE condition; in the host-driven loop it does not.
-// With `ev` (10 events) each kernel is bracketed by a pair of events.
-cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
-                                 cudaGraphConditionalHandle handle, int use_cond, int num_sms,
-                                 cudaStream_t st, cudaEvent_t *ev) {
+template <bool kMulti>
+cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
+                           cudaGraphConditionalHandle handle, int use_cond, int num_sms,
+                           cudaStream_t st, cudaEvent_t *ev) {
   cudaError_t e;
   int nb = (M.nslices + kRoundWarps - 1) / kRoundWarps;
   if (nb < 1) nb = 1;
   if (ev) cudaEventRecord(ev[0], st);
-  k_round<<<nb, kRoundWarps * 32, 0, st>>>(M, S);
+  k_round<kMulti><<<nb, kRoundWarps * 32, 0, st>>>(M, S);
   if (ev) cudaEventRecord(ev[1], st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (M.nsplit_rows > 0) {
     int nbc = (M.nsplit_rows + kCombineWarps - 1) / kCombineWarps;
     if (ev) cudaEventRecord(ev[2], st);
-    k_combine<<<nbc, kCombineWarps * 32, 0, st>>>(M, S);
+    k_combine<kMulti><<<nbc, kCombineWarps * 32, 0, st>>>(M, S);
     if (ev) cudaEventRecord(ev[3], st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int nbs = (M.nslices_split + kRoundWarps - 1) / kRoundWarps;
@@ -694,14 +752,26 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const ui
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[8], st);
-  k_cand_queue<<<num_sms * 8, 256, 0, st>>>(M, S);
+  k_cand_queue<kMulti><<<num_sms * 8, 256, 0, st>>>(M, S);
   if (ev) cudaEventRecord(ev[9], st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int nbf = grid_for(M.n, kFinishThreads, num_sms * 8);
   if (ev) cudaEventRecord(ev[6], st);
-  k_finish<<<nbf, kFinishThreads, 0, st>>>(S, vt_ws, M.n, handle, use_cond);
+  k_finish<kMulti><<<nbf, kFinishThreads, 0, st>>>(S, vt_ws, M.n, handle, use_cond);
   if (ev) cudaEventRecord(ev[7], st);
   return cudaGetLastError();
+}
+
+// Launches one round's kernels on `st`.  In the graph body (use_cond = 1)
+// k_finish sets the WHILE condition; in the host-driven loop it does not.
+// With `ev` (10 events) each kernel is bracketed by a pair of events.  A
+// problem set (S.I.ninst > 0) runs the per-problem variants.
+cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
+                                 cudaGraphConditionalHandle handle, int use_cond, int num_sms,
+                                 cudaStream_t st, cudaEvent_t *ev) {
+  if (S.I.ninst > 0)
+    return launch_round_t<true>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
+  return launch_round_t<false>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
 }
 
 cudaError_t launch_round_body(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,

@@ -32,6 +32,10 @@ struct dp_matrix {
   cudaGraphExec_t exec = nullptr;
   // batched nodes (allocated on the first dp_propagate_nodes call)
   struct BatchWs *batch = nullptr;
+  // problem sets (dp_matrix_load_set): first row / variable of each problem
+  int32_t ninst = 0;
+  std::vector<int32_t> row_off, var_off;
+  int32_t *h_inst = nullptr;  // pinned [3*ninst]: infeasible, rounds, status
 };
 
 // Workspace of dp_propagate_nodes for up to Bp_cap nodes per launch.
