@@ -57,7 +57,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["large", "medium", "tiny"], default="large")
-    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="row split length (0: chosen by the autotuner)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (chunk 256, 8 warps per block)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling captures only; the bench line uses 1.0)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -510,8 +513,17 @@ def run_ours(args):
     inst = make_workload(args.workload, args.scale)
     stream = torch.cuda.current_stream()
     ctx = dp.Context(local, stream)
-    mat = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, args.chunk,
+    tune = None
+    chunk, warps = args.chunk, 8
+    if not args.no_autotune and not args.chunk:
+        t0 = time.perf_counter()
+        tune = dp.dp_autotune(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.lb,
+                              inst.ub, inst.vartype, inst.lhs, inst.rhs, rounds=3)
+        tune["seconds"] = round(time.perf_counter() - t0, 1)
+        chunk, warps = tune["best"]["chunk"], tune["best"]["round_warps"]
+    mat = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, chunk,
                     lhs=inst.lhs, rhs=inst.rhs)
+    mat.set_launch(warps)
     info = mat.info()
     d_in = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in inst.problem()]
     d_lb = torch.empty(inst.n, dtype=torch.float64, device="cuda")
@@ -614,7 +626,8 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic (seeded; stands in for MIPLIB 2017)",
-               "config": {**describe(inst), "rounds_per_step": rounds, "chunk": args.chunk or 256,
+               "config": {**describe(inst), "rounds_per_step": rounds, "chunk": chunk or 256,
+                          "round_warps": warps, "autotune": tune,
                           "split_rows": info["split_rows"], "padded_slots": info["padded_slots"],
                           "round_us": round(per_round_us, 2),
                           "round_GBps_algorithmic": round((b_round + b_finish) / (per_round_us * 1e-6) / 1e9, 1),

@@ -161,6 +161,38 @@ int dp_matrix_load_set(dp_ctx *ctx, int32_t count, const int32_t *m,
 int dp_matrix_set_offsets(const dp_matrix *set, int32_t *count,
                           int32_t *row_off, int32_t *var_off);
 
+/* Warps per block of the round kernels (4 or 8; the default is 8): a launch
+ * shape the autotuner chooses.  Waits for the matrix's pending work. */
+int dp_matrix_set_launch(dp_matrix *mat, int32_t round_warps);
+
+typedef struct {
+  int32_t chunk;        /* row split length (dp_matrix_load's `chunk`) */
+  int32_t round_warps;  /* warps per block (dp_matrix_set_launch) */
+  float us_per_round;   /* measured device time of one round, microseconds */
+  int32_t reserved;
+} dp_tune_entry;
+
+/*
+ * Autotuner: times `rounds` rounds (from the given bounds) of the problem
+ * for every row split length in {64, 128, 256, 512, 1024} that gives a
+ * distinct layout (the long-row threshold of the paper's row bins,
+ * Sec. 3.2: longer rows are split and combined in a second pass) and every
+ * block shape {4, 8} warps, with CUDA events on each round kernel (the
+ * host-driven loop).  Arguments as dp_matrix_load_sides plus the problem of
+ * dp_propagate; lhs/rhs order the rows when they are host arrays.
+ * entries[max_entries] (may be NULL if 0) receive the measurements, *count
+ * their number, *best the fastest.  Loads and frees one matrix per
+ * distinct layout, so it costs several layout builds: run it once per
+ * matrix family and load with the best chunk and launch shape.
+ */
+int dp_autotune(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                const int64_t *row_ptr, const int32_t *col_idx,
+                const double *val, const double *lb, const double *ub,
+                const uint8_t *vartype, const double *lhs, const double *rhs,
+                const dp_params *params, int32_t rounds,
+                dp_tune_entry *entries, int32_t max_entries, int32_t *count,
+                dp_tune_entry *best);
+
 /* Frees a matrix; NULL is a no-op. */
 void dp_matrix_free(dp_matrix *mat);
 

@@ -30,7 +30,8 @@ DP_ERR_TIMEOUT = -6
 
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
-           "dp_matrix_load_sides", "dp_matrix_load_set", "dp_matrix_set_offsets", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
+           "dp_matrix_load_sides", "dp_matrix_load_set", "dp_matrix_set_offsets",
+           "dp_matrix_set_launch", "dp_autotune", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes", "dp_propagate_set",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
            "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
@@ -40,6 +41,11 @@ SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_ma
 class dp_params(C.Structure):
     _fields_ = [("max_rounds", C.c_int32), ("reserved0", C.c_int32), ("eps_int", C.c_double),
                 ("tau_rel", C.c_double), ("eps_feas", C.c_double), ("inf_threshold", C.c_double)]
+
+
+class dp_tune_entry(C.Structure):
+    _fields_ = [("chunk", C.c_int32), ("round_warps", C.c_int32), ("us_per_round", C.c_float),
+                ("reserved", C.c_int32)]
 
 
 class dp_server_config(C.Structure):
@@ -88,6 +94,12 @@ def lib() -> C.CDLL:
     L.dp_matrix_load_set.restype = C.c_int
     L.dp_matrix_set_offsets.argtypes = [vp, C.POINTER(i32), vp, vp]
     L.dp_matrix_set_offsets.restype = C.c_int
+    L.dp_matrix_set_launch.argtypes = [vp, i32]
+    L.dp_matrix_set_launch.restype = C.c_int
+    L.dp_autotune.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp,
+                              C.POINTER(dp_params), i32, C.POINTER(dp_tune_entry), i32,
+                              C.POINTER(i32), C.POINTER(dp_tune_entry)]
+    L.dp_autotune.restype = C.c_int
     L.dp_propagate_set.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp, vp,
                                    vp, vp]
     L.dp_propagate_set.restype = C.c_int
@@ -229,6 +241,10 @@ class Matrix:
         self.ctx = ctx
         self.m, self.n = int(m), int(n)
 
+    def set_launch(self, round_warps: int) -> None:
+        """Warps per block of the round kernels (4 or 8)."""
+        _check(lib().dp_matrix_set_launch(self.handle, int(round_warps)), "dp_matrix_set_launch")
+
     def info(self) -> dict:
         m, n, s = C.c_int32(), C.c_int32(), C.c_int32()
         nnz, pad = C.c_int64(), C.c_int64()
@@ -247,6 +263,30 @@ class Matrix:
 
     def __exit__(self, *a):
         self.close()
+
+
+def dp_matrix_set_launch(mat: Matrix, round_warps: int) -> None:
+    mat.set_launch(round_warps)
+
+
+def dp_autotune(ctx: Context, m: int, n: int, row_ptr, col_idx, val, lb, ub, vartype, lhs, rhs,
+                params: dp_params | None = None, rounds: int = 4) -> dict:
+    """Times `rounds` rounds of the problem for each row split length and
+    block shape; returns {"best": {...}, "entries": [...]}."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    ent = (dp_tune_entry * 16)()
+    cnt = C.c_int32()
+    best = dp_tune_entry()
+    nnz = int(row_ptr[-1]) if m > 0 else 0
+    _check(lib().dp_autotune(ctx.handle, int(m), int(n), nnz, _ptr(row_ptr), _ptr(col_idx),
+                             _ptr(val), _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs), _ptr(rhs),
+                             C.byref(params) if params is not None else None, int(rounds), ent,
+                             16, C.byref(cnt), C.byref(best)), "dp_autotune")
+    conv = lambda e: {"chunk": e.chunk, "round_warps": e.round_warps,
+                      "us_per_round": e.us_per_round}
+    return {"best": conv(best), "entries": [conv(ent[i]) for i in range(min(cnt.value, 16))]}
 
 
 class MatrixSet(Matrix):

@@ -248,6 +248,7 @@ int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row
   M.nslices = H.nslices;
   M.nslices_split = H.nslices_split;
   M.nsplit_rows = H.nsplit_rows;
+  M.round_warps = 8;
   mat->padded = (int64_t)H.val.size();
 #define TRY(x)                 \
   do {                         \
@@ -393,6 +394,19 @@ int dp_matrix_load_set(dp_ctx *ctx, int32_t count, const int32_t *m, const int32
   return load_impl(ctx, (int32_t)mt, (int32_t)nt, nzt, rp.data(), col.data(), vv.data(), chunk,
                    lhs ? sl.data() : nullptr, lhs ? sr.data() : nullptr, &row_off, &var_off,
                    out);
+}
+
+int dp_matrix_set_launch(dp_matrix *mat, int32_t round_warps) {
+  if (!mat || (round_warps != 4 && round_warps != 8)) return DP_ERR_INVALID_ARG;
+  if (mat->M.round_warps == round_warps) return DP_OK;
+  CUDA_TRY(cudaSetDevice(mat->ctx->device));
+  CUDA_TRY(cudaStreamSynchronize(mat->ctx->stream));
+  if (mat->exec) cudaGraphExecDestroy(mat->exec);
+  if (mat->graph) cudaGraphDestroy(mat->graph);
+  mat->exec = nullptr;
+  mat->graph = nullptr;
+  mat->M.round_warps = round_warps;
+  return build_graph(mat);
 }
 
 int dp_matrix_set_offsets(const dp_matrix *set, int32_t *count, int32_t *row_off,

@@ -93,7 +93,7 @@ struct DevMatrix {
   int32_t nslices;        // all slices
   int32_t nslices_split;  // slices [0, nslices_split) hold split-row chunks
   int32_t nsplit_rows;
-  int32_t pad;
+  int32_t round_warps;      // warps per block of the round kernel (4 or 8)
   const double *val;        // padded slot-major values
   const int32_t *col;       // padded slot-major column indices
   const int64_t *slice_off; // [nslices] element offset of each slice

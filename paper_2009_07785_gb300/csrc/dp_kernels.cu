@@ -245,12 +245,14 @@ __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
 
 // ------------------------------------------------------------- k_round --
 
-constexpr int kRoundWarps = 8;
+// Warps per block of k_round / k_cand_split: a launch shape the autotuner
+// chooses (4 or 8); the register budget per thread stays the same (24
+// resident warps per SM).
+constexpr int kRoundWarpsPerSM = 24;
 constexpr int kGroup = 4;         // slots per group in the activity loop
-constexpr int kRoundMinBlocks = 3;  // resident blocks per SM the register budget allows
 
-template <bool kMulti>
-__global__ void __launch_bounds__(kRoundWarps * 32, kRoundMinBlocks)
+template <bool kMulti, int kRoundWarps>
+__global__ void __launch_bounds__(kRoundWarps * 32, kRoundWarpsPerSM / kRoundWarps)
 k_round(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
@@ -489,6 +491,7 @@ k_combine(DevMatrix M, DevState S) {
 
 // --------------------------------------------------------- k_cand_split --
 
+template <int kRoundWarps>
 __global__ void __launch_bounds__(kRoundWarps * 32)
 k_cand_split(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
@@ -728,7 +731,7 @@ cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out, double
   return cudaGetLastError();
 }
 
-template <bool kMulti>
+template <bool kMulti, int kRoundWarps>
 cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
                            cudaGraphConditionalHandle handle, int use_cond, int num_sms,
                            cudaStream_t st, cudaEvent_t *ev) {
@@ -736,7 +739,7 @@ cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t 
   int nb = (M.nslices + kRoundWarps - 1) / kRoundWarps;
   if (nb < 1) nb = 1;
   if (ev) cudaEventRecord(ev[0], st);
-  k_round<kMulti><<<nb, kRoundWarps * 32, 0, st>>>(M, S);
+  k_round<kMulti, kRoundWarps><<<nb, kRoundWarps * 32, 0, st>>>(M, S);
   if (ev) cudaEventRecord(ev[1], st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (M.nsplit_rows > 0) {
@@ -747,7 +750,7 @@ cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int nbs = (M.nslices_split + kRoundWarps - 1) / kRoundWarps;
     if (ev) cudaEventRecord(ev[4], st);
-    k_cand_split<<<nbs, kRoundWarps * 32, 0, st>>>(M, S);
+    k_cand_split<kRoundWarps><<<nbs, kRoundWarps * 32, 0, st>>>(M, S);
     if (ev) cudaEventRecord(ev[5], st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -769,9 +772,12 @@ cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t 
 cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
                                  cudaGraphConditionalHandle handle, int use_cond, int num_sms,
                                  cudaStream_t st, cudaEvent_t *ev) {
+  const bool w4 = M.round_warps == 4;
   if (S.I.ninst > 0)
-    return launch_round_t<true>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
-  return launch_round_t<false>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
+    return w4 ? launch_round_t<true, 4>(M, S, vt_ws, handle, use_cond, num_sms, st, ev)
+              : launch_round_t<true, 8>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
+  return w4 ? launch_round_t<false, 4>(M, S, vt_ws, handle, use_cond, num_sms, st, ev)
+            : launch_round_t<false, 8>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
 }
 
 cudaError_t launch_round_body(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,

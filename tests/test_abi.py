@@ -87,3 +87,16 @@ def test_generator_is_deterministic():
     ax = np.array([np.dot(a.val[a.row_ptr[i]:a.row_ptr[i + 1]], a.xstar[a.col[a.row_ptr[i]:a.row_ptr[i + 1]]])
                    for i in range(a.m)])
     assert np.all(ax <= a.rhs) and np.all(ax >= a.lhs)
+
+
+def test_host_side_argument_checks(lib):
+    """Entry points reject null handles before touching a device."""
+    import paper_2009_07785_gb300 as dp
+
+    L = dp.lib()
+    assert L.dp_matrix_set_launch(None, 4) == dp.DP_ERR_INVALID_ARG
+    best = dp.dp_tune_entry()
+    assert L.dp_autotune(None, 0, 0, 0, None, None, None, None, None, None, None, None, None, 4,
+                         None, 0, None, best) == dp.DP_ERR_INVALID_ARG
+    assert L.dp_propagate_set(None, None, None, None, None, None, None, None, None, None, None,
+                              None, None) == dp.DP_ERR_INVALID_ARG

@@ -171,3 +171,31 @@ def test_large_scaled_side_ordered(gpu, orc):
                    lhs=inst.lhs, rhs=inst.rhs) as mat:
         replay(dp, ctx, mat, inst, orc)
         check_full(dp, ctx, mat, inst, orc, exact=False)
+
+
+def test_launch_shapes_bit_identical(gpu, orc):
+    """Both block shapes of the round kernels give the same bits."""
+    dp, ctx = gpu
+    inst = synth.tiny()
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        a = gpu_full(dp, ctx, mat, inst)
+        mat.set_launch(4)
+        b = gpu_full(dp, ctx, mat, inst)
+        check_full(dp, ctx, mat, inst, orc, exact=True)
+        mat.set_launch(8)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2].rounds == b[2].rounds
+
+
+def test_autotune_picks_a_measured_configuration(gpu, orc):
+    dp, ctx = gpu
+    inst = synth.medium(scale=0.05)
+    t = dp.dp_autotune(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.lb, inst.ub,
+                       inst.vartype, inst.lhs, inst.rhs, rounds=3)
+    us = [e["us_per_round"] for e in t["entries"]]
+    assert len(us) >= 4 and min(us) > 0 and t["best"]["us_per_round"] == min(us)
+    assert {e["round_warps"] for e in t["entries"]} == {4, 8}
+    b = t["best"]
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, b["chunk"],
+                   lhs=inst.lhs, rhs=inst.rhs) as mat:
+        mat.set_launch(b["round_warps"])
+        check_full(dp, ctx, mat, inst, orc, exact=False)
