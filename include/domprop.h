@@ -227,6 +227,23 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
                  double *ub_out, int32_t *infeasible, int32_t *rounds);
 
 /*
+ * dp_propagate with the whole round loop in one persistent kernel: a
+ * cooperative launch (all blocks resident) whose blocks separate the round's
+ * phases by grid barriers and read the loop condition after the last one --
+ * the device-driven loop of Sec. 3.7 without any per-round launch.  Same
+ * arguments, results and status as dp_propagate (single problems only;
+ * DP_ERR_INVALID_ARG for a problem set).  Its barrier waits are bounded:
+ * DP_ERR_TIMEOUT would report a barrier that did not complete (it cannot
+ * happen when the launch succeeds).
+ */
+int dp_propagate_persistent(dp_ctx *ctx, const dp_matrix *mat,
+                            const double *lb, const double *ub,
+                            const uint8_t *vartype, const double *lhs,
+                            const double *rhs, const dp_params *params,
+                            double *lb_out, double *ub_out,
+                            int32_t *infeasible, int32_t *rounds);
+
+/*
  * Propagates every problem of a set (dp_matrix_load_set) in one device-side
  * round loop.  lb, ub, vartype (length: total variables) and lhs, rhs
  * (total rows) are the problems' arrays concatenated in problem order

@@ -33,6 +33,7 @@ SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_ma
            "dp_matrix_load_sides", "dp_matrix_load_set", "dp_matrix_set_offsets",
            "dp_matrix_set_launch", "dp_autotune", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes", "dp_propagate_set",
+           "dp_propagate_persistent",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
            "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
            "dp_server_destroy")
@@ -103,6 +104,9 @@ def lib() -> C.CDLL:
     L.dp_propagate_set.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp, vp,
                                    vp, vp]
     L.dp_propagate_set.restype = C.c_int
+    L.dp_propagate_persistent.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp,
+                                          vp, C.POINTER(i32), C.POINTER(i32)]
+    L.dp_propagate_persistent.restype = C.c_int
     L.dp_matrix_free.argtypes = [vp]
     L.dp_matrix_free.restype = None
     L.dp_matrix_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
@@ -421,6 +425,23 @@ def dp_propagate(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs, params: d
                                    _ptr(lhs), _ptr(rhs), C.byref(params) if params is not None else None,
                                    _ptr(lb_out), _ptr(ub_out), C.byref(inf), C.byref(rounds)),
                 "dp_propagate")
+    return Result(lb_out, ub_out, inf.value, rounds.value, rc)
+
+
+def dp_propagate_persistent(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
+                            params: dp_params | None = None, lb_out=None, ub_out=None) -> Result:
+    """Same as dp_propagate, with the round loop in one persistent
+    (cooperative) kernel instead of the graph's WHILE node."""
+    n = mat.n
+    if lb_out is None:
+        lb_out = _like(lb, n)
+    if ub_out is None:
+        ub_out = _like(lb, n)
+    inf, rounds = C.c_int32(), C.c_int32()
+    rc = _check(lib().dp_propagate_persistent(
+        ctx.handle, mat.handle, _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs), _ptr(rhs),
+        C.byref(params) if params is not None else None, _ptr(lb_out), _ptr(ub_out),
+        C.byref(inf), C.byref(rounds)), "dp_propagate_persistent")
     return Result(lb_out, ub_out, inf.value, rounds.value, rc)
 
 

@@ -281,6 +281,7 @@ int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row
   TRY(dev_alloc(mat, &S.rowsum, (size_t)H.nslices * dp::kSliceW));
   TRY(dev_alloc(mat, &S.side, (size_t)H.nslices * dp::kSliceW));
   TRY(dev_alloc(mat, &S.ctrl, 1));
+  TRY(dev_alloc(mat, &S.bar, 2));
   TRY(dev_alloc(mat, &mat->vt_ws, (size_t)n));
   TRY(dev_alloc(mat, &mat->st_lb, (size_t)n));
   TRY(dev_alloc(mat, &mat->st_ub, (size_t)n));
@@ -524,6 +525,27 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
   rc = begin_call(ctx, mat, lb, ub, vartype, lhs, rhs, p);
   if (rc) return rc;
   if (p.max_rounds > 0) CUDA_TRY(cudaGraphLaunch(mat->exec, ctx->stream));
+  return end_call(ctx, mat, p, lb_out, ub_out, infeasible, rounds);
+}
+
+int dp_propagate_persistent(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
+                            const double *ub, const uint8_t *vartype, const double *lhs,
+                            const double *rhs, const dp_params *params, double *lb_out,
+                            double *ub_out, int32_t *infeasible, int32_t *rounds) {
+  dp_params p;
+  int rc = check_call(ctx, cmat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
+                      infeasible, rounds, &p);
+  if (rc) return rc;
+  if (cmat->ninst > 0) return DP_ERR_INVALID_ARG;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess ||
+      !coop)
+    return DP_ERR_CUDA;
+  dp_matrix *mat = const_cast<dp_matrix *>(cmat);
+  rc = begin_call(ctx, mat, lb, ub, vartype, lhs, rhs, p);
+  if (rc) return rc;
+  if (p.max_rounds > 0)
+    CUDA_TRY(dp::launch_persistent(mat->M, mat->S, mat->vt_ws, ctx->num_sms, ctx->stream));
   return end_call(ctx, mat, p, lb_out, ub_out, infeasible, rounds);
 }
 

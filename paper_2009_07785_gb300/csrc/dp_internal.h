@@ -84,6 +84,8 @@ struct Ctrl {
   int32_t err;          // 0, or a DP_ERR_* code found by the prologue
   uint32_t blocks_done; // arrival counter of the last kernel of a round
   int32_t qcount;       // entries appended to the candidate queue this round
+  int32_t cont;         // the last round asked for another one
+  int32_t pad;
   double eps_int, tau_rel, eps_feas, inf_thr;
 };
 
@@ -131,6 +133,7 @@ struct DevState {
   Partial *part;        // [nslices_split*32]
   RowTot *rowtot;       // [nsplit_rows]
   Ctrl *ctrl;
+  unsigned *bar;        // [2] grid barrier of the persistent loop: arrivals, generation
   InstState I;          // problem sets only
 };
 

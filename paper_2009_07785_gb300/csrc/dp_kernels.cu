@@ -210,14 +210,11 @@ __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t,
 
 // ---------------------------------------------------------- k_cand_queue --
 
-// Evaluates the queued nonzeros, one per thread (grid-stride).
+// Evaluates one queued nonzero (thread-level).
 template <bool kMulti>
-__global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
-  const Ctrl *ctrl = S.ctrl;
-  if (ctrl->err) return;
-  const int32_t cnt = ctrl->qcount;
-  const Ctrl prm = *ctrl;
-  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void cand_entry(const DevMatrix &M, const DevState &S,
+                                           const Ctrl &prm, int32_t e) {
+  {
     const CandEntry E = S.queue[e];
     const uint32_t c = E.cs >> 2;
     const RowSum rs = S.rowsum[c];
@@ -243,6 +240,17 @@ __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
   }
 }
 
+// Evaluates the queued nonzeros, one per thread (grid-stride).
+template <bool kMulti>
+__global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
+  const Ctrl *ctrl = S.ctrl;
+  if (ctrl->err) return;
+  const int32_t cnt = ctrl->qcount;
+  const Ctrl prm = *ctrl;
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x)
+    cand_entry<kMulti>(M, S, prm, e);
+}
+
 // ------------------------------------------------------------- k_round --
 
 // Warps per block of k_round / k_cand_split: a launch shape the autotuner
@@ -251,15 +259,11 @@ __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
 constexpr int kRoundWarpsPerSM = 24;
 constexpr int kGroup = 4;         // slots per group in the activity loop
 
-template <bool kMulti, int kRoundWarps>
-__global__ void __launch_bounds__(kRoundWarps * 32, kRoundWarpsPerSM / kRoundWarps)
-k_round(DevMatrix M, DevState S) {
+// One slice of the round (warp-level: the 32 lanes are its 32 chunks).
+template <bool kMulti>
+__device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &S, int slice) {
   const Ctrl *ctrl = S.ctrl;
-  if (ctrl->err) return;
-  const int wib = threadIdx.x >> 5;
-  const int slice = blockIdx.x * kRoundWarps + wib;
   const int lane = threadIdx.x & 31;
-  if (slice >= M.nslices) return;  // warp-uniform
   const int64_t c = (int64_t)slice * kSliceW + lane;
   const int32_t lenf = M.chunk_len[c];
   int32_t len = lenf & kLenMask;
@@ -391,19 +395,25 @@ k_round(DevMatrix M, DevState S) {
   warp_enqueue(rv, t, mininf, maxinf, len, c, sbase, M.val, M.col, S);
 }
 
+template <bool kMulti, int kRoundWarps>
+__global__ void __launch_bounds__(kRoundWarps * 32, kRoundWarpsPerSM / kRoundWarps)
+k_round(DevMatrix M, DevState S) {
+  if (S.ctrl->err) return;
+  const int slice = blockIdx.x * kRoundWarps + (threadIdx.x >> 5);
+  if (slice >= M.nslices) return;  // warp-uniform
+  round_slice<kMulti>(M, S, slice);
+}
+
 // ------------------------------------------------------------ k_combine --
 
 constexpr int kCombineWarps = 8;
 constexpr int kCombineShort = 4;  // rows with at most this many pieces: one lane
 
+// One split row (warp-level).
 template <bool kMulti>
-__global__ void __launch_bounds__(kCombineWarps * 32)
-k_combine(DevMatrix M, DevState S) {
+__device__ __forceinline__ void combine_row(const DevMatrix &M, const DevState &S, int w) {
   const Ctrl *ctrl = S.ctrl;
-  if (ctrl->err) return;
-  const int w = blockIdx.x * kCombineWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (w >= M.nsplit_rows) return;
   const int32_t cb = M.split_cbeg[w], ce = M.split_cbeg[w + 1];
   int32_t *inf_flag = &S.ctrl->infeasible;
   if (kMulti) {
@@ -489,17 +499,21 @@ k_combine(DevMatrix M, DevState S) {
   S.rowtot[w] = rt;
 }
 
+template <bool kMulti>
+__global__ void __launch_bounds__(kCombineWarps * 32)
+k_combine(DevMatrix M, DevState S) {
+  if (S.ctrl->err) return;
+  const int w = blockIdx.x * kCombineWarps + (threadIdx.x >> 5);
+  if (w >= M.nsplit_rows) return;  // warp-uniform
+  combine_row<kMulti>(M, S, w);
+}
+
 // --------------------------------------------------------- k_cand_split --
 
-template <int kRoundWarps>
-__global__ void __launch_bounds__(kRoundWarps * 32)
-k_cand_split(DevMatrix M, DevState S) {
-  const Ctrl *ctrl = S.ctrl;
-  if (ctrl->err) return;
-  const int wib = threadIdx.x >> 5;
-  const int slice = blockIdx.x * kRoundWarps + wib;
+// Candidates of the active split rows' chunks of one slice (warp-level).
+__device__ __forceinline__ void cand_split_slice(const DevMatrix &M, const DevState &S,
+                                                 int slice) {
   const int lane = threadIdx.x & 31;
-  if (slice >= M.nslices_split) return;  // warp-uniform
   const int64_t c = (int64_t)slice * kSliceW + lane;
   const int32_t sidx = M.chunk_sidx[c];
   RowView rv;
@@ -535,6 +549,15 @@ k_cand_split(DevMatrix M, DevState S) {
   warp_enqueue(rv, t, cmin, cmax, len, c, sbase, M.val, M.col, S);
 }
 
+template <int kRoundWarps>
+__global__ void __launch_bounds__(kRoundWarps * 32)
+k_cand_split(DevMatrix M, DevState S) {
+  if (S.ctrl->err) return;
+  const int slice = blockIdx.x * kRoundWarps + (threadIdx.x >> 5);
+  if (slice >= M.nslices_split) return;  // warp-uniform
+  cand_split_slice(M, S, slice);
+}
+
 // ------------------------------------------------------------- k_finish --
 
 constexpr int kFinishThreads = 256;
@@ -542,49 +565,38 @@ constexpr int kFinishThreads = 256;
 // Ends a round: the next state becomes the current one.  The last block to
 // arrive (threadfence-reduction pattern; nobody waits) counts the round and
 // sets the WHILE condition of the enclosing graph node.
+// Commits one variable's next state (thread-level): the keys become the
+// record the next round gathers; crossing bounds flag infeasibility.
 template <bool kMulti>
-__global__ void __launch_bounds__(kFinishThreads)
-k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHandle handle,
-         int use_cond) {
-  Ctrl *ctrl = S.ctrl;
-  const int32_t err = ctrl->err;
-  const double eps_feas = ctrl->eps_feas;
-  const float tau_dn = f32_dn(ctrl->tau_rel), eps_dn = f32_dn(ctrl->eps_int);
-  if (!err) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-      int32_t *inf_flag = &ctrl->infeasible;
-      if (kMulti) {
-        const int32_t inst = S.I.var_inst[j];
-        if (S.I.done[inst]) continue;  // a stopped problem keeps its bounds
-        inf_flag = &S.I.infeasible[inst];
-      }
-      longlong2 kk = reinterpret_cast<const longlong2 *>(S.keys)[j];
-      double L = val_of_key(kk.x), U = val_of_key(kk.y);
-      uint32_t vt = vartype[j] ? 1u : 0u;
-      if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
-        bool cross = vt ? (L > U) : (L > U + eps_feas * fmax(1.0, fabs(U)));
-        if (cross) set_flag(inf_flag);
-      }
-      write_var(S.rec + j, L, U, vt, tau_dn, eps_dn);
-    }
+__device__ __forceinline__ void finish_var(const DevState &S, const uint8_t *vartype, int64_t j,
+                                           double eps_feas, float tau_dn, float eps_dn) {
+  int32_t *inf_flag = &S.ctrl->infeasible;
+  if (kMulti) {
+    const int32_t inst = S.I.var_inst[j];
+    if (S.I.done[inst]) return;  // a stopped problem keeps its bounds
+    inf_flag = &S.I.infeasible[inst];
   }
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
-    s_last = prev == gridDim.x - 1;
+  longlong2 kk = reinterpret_cast<const longlong2 *>(S.keys)[j];
+  double L = val_of_key(kk.x), U = val_of_key(kk.y);
+  uint32_t vt = vartype[j] ? 1u : 0u;
+  if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
+    bool cross = vt ? (L > U) : (L > U + eps_feas * fmax(1.0, fabs(U)));
+    if (cross) set_flag(inf_flag);
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  volatile Ctrl *vc = ctrl;
+  write_var(S.rec + j, L, U, vt, tau_dn, eps_dn);
+}
+
+// Ends a round (one block, all threads; after every variable is committed):
+// counts the round, resets the round's counters and returns whether to
+// continue.  For a problem set each problem counts its rounds and stops on
+// its own (no change, infeasible, or the cap); the loop runs while any
+// problem is live.
+template <bool kMulti>
+__device__ __forceinline__ int decide_round(const DevState &S) {
+  volatile Ctrl *vc = S.ctrl;
   const int32_t r = vc->round + 1;
   int32_t cont;
   if (kMulti) {
-    // each problem counts its rounds and stops on its own (no change,
-    // infeasible, or the cap); the loop runs while any problem is live
     volatile int32_t *ch = S.I.changed, *inf = S.I.infeasible, *dn = S.I.done;
     int live = 0;
     for (int i = threadIdx.x; i < S.I.ninst; i += blockDim.x) {
@@ -604,20 +616,125 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHand
     }
     live = __syncthreads_or(live);
     cont = (live && !vc->err && r < vc->max_rounds) ? 1 : 0;
-    if (threadIdx.x != 0) return;
-    vc->last_changed = live;
+    if (threadIdx.x == 0) vc->last_changed = live;
   } else {
-    if (threadIdx.x != 0) return;
-    int32_t chg = vc->changed;
+    const int32_t chg = vc->changed;
     cont = (chg && !vc->infeasible && !vc->err && r < vc->max_rounds) ? 1 : 0;
-    vc->last_changed = chg;
+    __syncthreads();
+    if (threadIdx.x == 0) vc->last_changed = chg;
   }
-  vc->round = r;
-  vc->changed = 0;
-  vc->qcount = 0;
-  vc->blocks_done = 0;
+  if (threadIdx.x == 0) {
+    vc->round = r;
+    vc->changed = 0;
+    vc->qcount = 0;
+    vc->cont = cont;
+    __threadfence();
+  }
+  return cont;
+}
+
+// Ends a round: every variable's next state becomes the current one.  The
+// last block to arrive (threadfence-reduction pattern; nobody waits) decides
+// whether to loop and sets the WHILE condition of the enclosing graph node.
+template <bool kMulti>
+__global__ void __launch_bounds__(kFinishThreads)
+k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHandle handle,
+         int use_cond) {
+  Ctrl *ctrl = S.ctrl;
+  const int32_t err = ctrl->err;
+  const double eps_feas = ctrl->eps_feas;
+  const float tau_dn = f32_dn(ctrl->tau_rel), eps_dn = f32_dn(ctrl->eps_int);
+  if (!err)
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+      finish_var<kMulti>(S, vartype, j, eps_feas, tau_dn, eps_dn);
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
   __threadfence();
-  if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
+  const int cont = decide_round<kMulti>(S);
+  if (threadIdx.x == 0) {
+    ctrl->blocks_done = 0;
+    __threadfence();
+    if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
+  }
+}
+
+// ------------------------------------------------------- persistent loop --
+//
+// The whole round loop as one cooperative launch (every block resident):
+// the round's phases are separated by grid barriers instead of kernel
+// boundaries, and the loop condition is read by every block after the last
+// barrier of a round -- the paper's device-driven loop (Sec. 3.7) as a
+// single persistent kernel, measured against the graph's WHILE node.
+
+constexpr int kPersistThreads = 256;
+constexpr long long kBarrierSpins = 1ll << 25;  // ~2 s of 64 ns sleeps
+
+// Grid-wide barrier (sense by generation count).  Bounded: a block that
+// waits too long records DP_ERR_TIMEOUT and leaves; every block returns
+// false once an error is recorded.  Cannot deadlock under a cooperative
+// launch, which guarantees that all blocks are resident.
+__device__ __forceinline__ bool grid_sync(const DevState &S) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = S.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(S.bar, 1u) == gridDim.x - 1) {
+      S.bar[0] = 0u;  // every block has arrived; none leaves before gen moves
+      __threadfence();
+      atomicAdd(S.bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > kBarrierSpins) {
+          atomicExch(&S.ctrl->err, DP_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ((volatile Ctrl *)S.ctrl)->err == 0;
+}
+
+__global__ void __launch_bounds__(kPersistThreads, kRoundWarpsPerSM / (kPersistThreads / 32))
+k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
+  if (((volatile Ctrl *)S.ctrl)->err) return;  // set before the launch: uniform
+  const Ctrl prm = *S.ctrl;  // parameters (constant during the run)
+  const float tau_dn = f32_dn(prm.tau_rel), eps_dn = f32_dn(prm.eps_int);
+  const int wpb = kPersistThreads / 32;
+  const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (;;) {
+    for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false>(M, S, sl);
+    if (!grid_sync(S)) return;
+    if (M.nsplit_rows > 0) {
+      for (int w = gw; w < M.nsplit_rows; w += nw) combine_row<false>(M, S, w);
+      if (!grid_sync(S)) return;
+      for (int sl = gw; sl < M.nslices_split; sl += nw) cand_split_slice(M, S, sl);
+      if (!grid_sync(S)) return;
+    }
+    const int32_t cnt = ((volatile Ctrl *)S.ctrl)->qcount;
+    for (int64_t e = gt; e < cnt; e += nt) cand_entry<false>(M, S, prm, (int32_t)e);
+    if (!grid_sync(S)) return;
+    for (int64_t j = gt; j < M.n; j += nt)
+      finish_var<false>(S, vartype, j, prm.eps_feas, tau_dn, eps_dn);
+    if (!grid_sync(S)) return;
+    if (blockIdx.x == 0) decide_round<false>(S);
+    if (!grid_sync(S)) return;
+    if (!((volatile Ctrl *)S.ctrl)->cont) return;
+  }
 }
 
 // ------------------------------------------------------ prologue/epilogue --
@@ -778,6 +895,22 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const ui
               : launch_round_t<true, 8>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
   return w4 ? launch_round_t<false, 4>(M, S, vt_ws, handle, use_cond, num_sms, st, ev)
             : launch_round_t<false, 8>(M, S, vt_ws, handle, use_cond, num_sms, st, ev);
+}
+
+cudaError_t launch_persistent(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
+                              int num_sms, cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent,
+                                                                kPersistThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  if ((e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
+  DevMatrix m = M;
+  DevState s = S;
+  const uint8_t *vt = vt_ws;
+  void *args[] = {&m, &s, &vt};
+  return cudaLaunchCooperativeKernel((const void *)k_persistent, dim3(num_sms * per_sm),
+                                     dim3(kPersistThreads), args, 0, st);
 }
 
 cudaError_t launch_round_body(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,

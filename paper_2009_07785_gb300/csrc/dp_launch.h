@@ -29,6 +29,11 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S,
                                  int use_cond, int num_sms, cudaStream_t st,
                                  cudaEvent_t *ev);
 
+// The whole round loop as one cooperative (persistent) launch on `st`
+// (single problems only).
+cudaError_t launch_persistent(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
+                              int num_sms, cudaStream_t st);
+
 // Batched branch-and-bound nodes (dp_batch.cu).  The prologue normalises
 // `count` node-major bound vectors (lb[node*n + j]) into the node-minor
 // state; the epilogue writes them back node-major.

@@ -199,3 +199,42 @@ def test_autotune_picks_a_measured_configuration(gpu, orc):
                    lhs=inst.lhs, rhs=inst.rhs) as mat:
         mat.set_launch(b["round_warps"])
         check_full(dp, ctx, mat, inst, orc, exact=False)
+
+
+def test_persistent_loop_bit_exact(gpu, orc):
+    """The persistent (cooperative) round loop gives the graph loop's bits
+    and the oracle's (tiny: bit-exact) results, including the round count,
+    the cap status and infeasibility."""
+    dp, ctx = gpu
+    inst = synth.tiny()
+    d = [dev(a) for a in (inst.lb, inst.ub, inst.vartype, inst.lhs, inst.rhs)]
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        r = dp.dp_propagate_persistent(ctx, mat, *d)
+        o = orc.propagate_instance(inst)
+        assert r.rounds == o.rounds and r.infeasible == o.infeasible
+        assert np.array_equal(host(r.lb), o.lb) and np.array_equal(host(r.ub), o.ub)
+        for q in ({"max_rounds": 2}, {"max_rounds": 0}):
+            rp = dp.dp_propagate_persistent(ctx, mat, *d, params=dp.dp_params_default(**q))
+            rg = dp.dp_propagate(ctx, mat, *d, params=dp.dp_params_default(**q))
+            assert rp.rounds == rg.rounds and rp.status == rg.status
+            assert np.array_equal(host(rp.lb), host(rg.lb))
+    LB, UB = synth.node_bounds(inst, 6, seed=11, lo_frac=0.05, hi_frac=0.2)
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        for b in range(6):
+            rp = dp.dp_propagate_persistent(ctx, mat, dev(LB[b]), dev(UB[b]), *d[2:])
+            rg = dp.dp_propagate(ctx, mat, dev(LB[b]), dev(UB[b]), *d[2:])
+            assert rp.rounds == rg.rounds and rp.infeasible == rg.infeasible
+            assert np.array_equal(host(rp.lb), host(rg.lb)) and np.array_equal(host(rp.ub), host(rg.ub))
+
+
+def test_persistent_loop_large_scaled_equals_graph(gpu):
+    dp, ctx = gpu
+    inst = synth.large(scale=0.05)
+    d = [dev(a) for a in (inst.lb, inst.ub, inst.vartype, inst.lhs, inst.rhs)]
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
+                   lhs=inst.lhs, rhs=inst.rhs) as mat:
+        assert mat.info()["split_rows"] > 0
+        rg = dp.dp_propagate(ctx, mat, *d)
+        rp = dp.dp_propagate_persistent(ctx, mat, *d)
+        assert rp.rounds == rg.rounds and rp.infeasible == rg.infeasible
+        assert np.array_equal(host(rp.lb), host(rg.lb)) and np.array_equal(host(rp.ub), host(rg.ub))
