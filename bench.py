@@ -15,6 +15,8 @@ roofline: the activity/candidate kernel (k_round), algorithmic bytes
           with the host-driven loop variant right after the timed region.
 cpu_baseline / --impl reference: the CPU oracle (one thread) on a bounded
           number of rounds of the same workload.
+persistent_loop: the same propagation with the round loop in one
+          cooperative kernel (dp_propagate_persistent) instead of the graph.
 batched_nodes: 256 branch-and-bound node bound vectors over the medium
           matrix (m=200k, ~2M nonzeros) propagated by one dp_propagate_nodes
           call, against the plain loop of one dp_propagate call per node.
@@ -66,6 +68,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-persistent", action="store_true",
+                    help="skip the persistent-kernel round loop measurement")
     ap.add_argument("--no-nodes", action="store_true",
                     help="skip the batched branch-and-bound node measurement")
     ap.add_argument("--nodes-only", action="store_true",
@@ -563,6 +567,23 @@ def run_ours(args):
     split = info["split_rows"] > 0
     launches = args.steps * (2 + (4 if split else 2) * rounds)
 
+    # the same propagation with the loop in one persistent (cooperative) kernel
+    persistent = None
+    if not args.no_persistent:
+        for _ in range(2):
+            rp = dp.dp_propagate_persistent(ctx, mat, *d_in, lb_out=d_lb, ub_out=d_ub)
+        kp = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(kp):
+            rp = dp.dp_propagate_persistent(ctx, mat, *d_in, lb_out=d_lb, ub_out=d_ub)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / kp
+        assert rp.rounds == rounds
+        persistent = {"ms_per_step": round(pms, 3), "value": inst.nnz * rounds / (pms * 1e-3),
+                      "graph_ms_per_step": round(ms / args.steps, 3), "steps": kp}
+
     # per-kernel CUDA-event timings with the host-driven loop (same kernels, same data)
     hl = dp.dp_propagate_hostloop(ctx, mat, *d_in, lb_out=d_lb, ub_out=d_ub)
     t_hl0 = time.perf_counter()
@@ -636,7 +657,8 @@ def run_ours(args):
                           "l2": "no flush: the matrix streamed each round (0.36 GB) exceeds the 129 MB L2",
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk, "batched_nodes": nodes, "batched_matrices": sets,
+               "clocks": clk, "persistent_loop": persistent, "batched_nodes": nodes,
+               "batched_matrices": sets,
                "serving": serving}
         print(json.dumps(out))
     mat.close()

@@ -707,7 +707,9 @@ __device__ __forceinline__ bool grid_sync(const DevState &S) {
   return ((volatile Ctrl *)S.ctrl)->err == 0;
 }
 
-__global__ void __launch_bounds__(kPersistThreads, kRoundWarpsPerSM / (kPersistThreads / 32))
+// Two resident blocks per SM: the union of all phases needs more registers
+// than three blocks allow (spills), and fewer resident warps hide less latency.
+__global__ void __launch_bounds__(kPersistThreads, 2)
 k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
   if (((volatile Ctrl *)S.ctrl)->err) return;  // set before the launch: uniform
   const Ctrl prm = *S.ctrl;  // parameters (constant during the run)
