@@ -165,6 +165,18 @@ int dp_matrix_set_offsets(const dp_matrix *set, int32_t *count,
  * shape the autotuner chooses.  Waits for the matrix's pending work. */
 int dp_matrix_set_launch(dp_matrix *mat, int32_t round_warps);
 
+/* Lossless value compression: when every coefficient of a loaded matrix is
+ * an integer in [-127, 127] the library also keeps the values as int8, and
+ * with on = 1 the single-instance round kernels read those (1 byte per
+ * value instead of 8; the binary64 value is rebuilt exactly on the integer
+ * pipe); on = 0 (the default) reads the binary64 values.  *active (may be
+ * NULL) tells whether the kernels now read the int8 copy.  Results are
+ * identical either way.  On GB300 the round kernel is bound by gathers and
+ * instruction issue rather than by the value stream, and the conversion
+ * made it slower, hence off by default.  Waits for the matrix's pending
+ * work. */
+int dp_matrix_set_compression(dp_matrix *mat, int32_t on, int32_t *active);
+
 typedef struct {
   int32_t chunk;        /* row split length (dp_matrix_load's `chunk`) */
   int32_t round_warps;  /* warps per block (dp_matrix_set_launch) */
@@ -173,12 +185,15 @@ typedef struct {
 } dp_tune_entry;
 
 /*
- * Autotuner: times `rounds` rounds (from the given bounds) of the problem
+ * Autotuner: times `rounds` rounds (from the given bounds; rounds <= 0: the
+ * whole propagation, to the fixed point or params' cap) of the problem
  * for every row split length in {64, 128, 256, 512, 1024} that gives a
  * distinct layout (the long-row threshold of the paper's row bins,
  * Sec. 3.2: longer rows are split and combined in a second pass) and every
  * block shape {4, 8} warps, with CUDA events on each round kernel (the
- * host-driven loop).  Arguments as dp_matrix_load_sides plus the problem of
+ * host-driven loop; the best of three timed calls; value compression off).
+ * Arguments as
+ * dp_matrix_load_sides plus the problem of
  * dp_propagate; lhs/rhs order the rows when they are host arrays.
  * entries[max_entries] (may be NULL if 0) receive the measurements, *count
  * their number, *best the fastest.  Loads and frees one matrix per

@@ -31,7 +31,7 @@ DP_ERR_TIMEOUT = -6
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
            "dp_matrix_load_sides", "dp_matrix_load_set", "dp_matrix_set_offsets",
-           "dp_matrix_set_launch", "dp_autotune", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
+           "dp_matrix_set_launch", "dp_matrix_set_compression", "dp_autotune", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes", "dp_propagate_set",
            "dp_propagate_persistent",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
@@ -97,6 +97,8 @@ def lib() -> C.CDLL:
     L.dp_matrix_set_offsets.restype = C.c_int
     L.dp_matrix_set_launch.argtypes = [vp, i32]
     L.dp_matrix_set_launch.restype = C.c_int
+    L.dp_matrix_set_compression.argtypes = [vp, i32, C.POINTER(i32)]
+    L.dp_matrix_set_compression.restype = C.c_int
     L.dp_autotune.argtypes = [vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp,
                               C.POINTER(dp_params), i32, C.POINTER(dp_tune_entry), i32,
                               C.POINTER(i32), C.POINTER(dp_tune_entry)]
@@ -249,6 +251,14 @@ class Matrix:
         """Warps per block of the round kernels (4 or 8)."""
         _check(lib().dp_matrix_set_launch(self.handle, int(round_warps)), "dp_matrix_set_launch")
 
+    def set_compression(self, on: bool) -> bool:
+        """Reads the int8 copy of small-integer coefficients (lossless) when
+        on and available; returns whether it is active."""
+        act = C.c_int32()
+        _check(lib().dp_matrix_set_compression(self.handle, 1 if on else 0, C.byref(act)),
+               "dp_matrix_set_compression")
+        return bool(act.value)
+
     def info(self) -> dict:
         m, n, s = C.c_int32(), C.c_int32(), C.c_int32()
         nnz, pad = C.c_int64(), C.c_int64()
@@ -271,6 +281,10 @@ class Matrix:
 
 def dp_matrix_set_launch(mat: Matrix, round_warps: int) -> None:
     mat.set_launch(round_warps)
+
+
+def dp_matrix_set_compression(mat: Matrix, on: bool) -> bool:
+    return mat.set_compression(on)
 
 
 def dp_autotune(ctx: Context, m: int, n: int, row_ptr, col_idx, val, lb, ub, vartype, lhs, rhs,

@@ -259,6 +259,10 @@ int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row
     }                          \
   } while (0)
   TRY(upload(mat, H.val, &M.val, st));
+  if (!H.val8.empty()) {
+    TRY(upload(mat, H.val8, &mat->val8, st));
+    M.val8 = nullptr;  // off by default: measured slower on GB300 (see the header)
+  }
   TRY(upload(mat, H.col, &M.col, st));
   TRY(upload(mat, H.slice_off, &M.slice_off, st));
   TRY(upload(mat, H.slice_len, &M.slice_len, st));
@@ -408,6 +412,24 @@ int dp_matrix_set_launch(dp_matrix *mat, int32_t round_warps) {
   mat->graph = nullptr;
   mat->M.round_warps = round_warps;
   return build_graph(mat);
+}
+
+int dp_matrix_set_compression(dp_matrix *mat, int32_t on, int32_t *active) {
+  if (!mat) return DP_ERR_INVALID_ARG;
+  const int8_t *want = (on && mat->val8) ? mat->val8 : nullptr;
+  if (want != mat->M.val8) {
+    CUDA_TRY(cudaSetDevice(mat->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(mat->ctx->stream));
+    if (mat->exec) cudaGraphExecDestroy(mat->exec);
+    if (mat->graph) cudaGraphDestroy(mat->graph);
+    mat->exec = nullptr;
+    mat->graph = nullptr;
+    mat->M.val8 = want;
+    int rc = build_graph(mat);
+    if (rc) return rc;
+  }
+  if (active) *active = mat->M.val8 ? 1 : 0;
+  return DP_OK;
 }
 
 int dp_matrix_set_offsets(const dp_matrix *set, int32_t *count, int32_t *row_off,

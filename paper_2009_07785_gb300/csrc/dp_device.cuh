@@ -52,6 +52,25 @@ __device__ __forceinline__ bool d_is_posinf(double x) {
   dsplit(x, lo, hi);
   return (hi == 0x7FF00000u) & (lo == 0u);
 }
+// The binary64 value of a nonzero integer v with |v| <= 127, assembled on
+// the integer pipe from the IEEE 754 fields: sign, exponent 1023 + e with
+// e = floor(log2|v|), and the bits of |v| below its leading one shifted to
+// the top of the 52-bit fraction.  Exact.
+__device__ __forceinline__ double small_int_to_double(int v) {
+  const unsigned long long s = v < 0 ? 1ull : 0ull;
+  const unsigned m = (unsigned)(v < 0 ? -v : v);
+  const int e = 31 - __clz(m);
+  const unsigned long long frac = (unsigned long long)(m - (1u << e)) << (52 - e);
+  return __longlong_as_double(
+      (long long)((s << 63) | ((unsigned long long)(1023 + e) << 52) | frac));
+}
+// Coefficient at element `off` of the sliced layout: from the int8 copy
+// when the matrix has one (1 byte per value instead of 8), streamed.
+__device__ __forceinline__ double ld_coef(const DevMatrix &M, int64_t off) {
+  if (M.val8) return small_int_to_double((int)__ldcs(M.val8 + off));
+  return __ldcs(M.val + off);
+}
+
 // coefficient sign without a binary64 comparison (coefficients are nonzero)
 __device__ __forceinline__ bool d_pos(double a) {
   unsigned lo, hi;

@@ -97,6 +97,8 @@ struct DevMatrix {
   int32_t nsplit_rows;
   int32_t round_warps;      // warps per block of the round kernel (4 or 8)
   const double *val;        // padded slot-major values
+  const int8_t *val8;       // the same values as int8 when all are small
+                            // integers and compression is on, else null
   const int32_t *col;       // padded slot-major column indices
   const int64_t *slice_off; // [nslices] element offset of each slice
   const int32_t *slice_len; // [nslices] slots in each slice

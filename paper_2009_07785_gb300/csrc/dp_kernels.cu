@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cfloat>
+#include <type_traits>
 
 #include "dp_device.cuh"
 #include "dp_internal.h"
@@ -121,7 +122,7 @@ __device__ __forceinline__ Top2 top2_init() {
 // this (warp collectives).
 __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t, int chunk_mininf,
                                              int chunk_maxinf, int32_t mylen, int64_t chunk_slot,
-                                             int64_t slice_off_elems, const double *val,
+                                             int64_t slice_off_elems, const DevMatrix &M,
                                              const int32_t *col, const DevState &S) {
   const int lane = threadIdx.x & 31;
   const bool act = mine.act != 0;
@@ -177,7 +178,7 @@ __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t,
   int maxlen = len;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kFull, maxlen, o));
-  const double *vp = val + slice_off_elems + lane;
+  const int64_t vo = slice_off_elems + lane;
   const int32_t *cp = col + slice_off_elems + lane;
   for (int k = 0; k < maxlen; k += 4) {
     double a[4];
@@ -187,7 +188,7 @@ __device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t,
       a[u] = 1.0;
       j[u] = 0;
       if (k + u < len) {
-        a[u] = vp[(int64_t)(k + u) * kSliceW];
+        a[u] = ld_coef(M, vo + (int64_t)(k + u) * kSliceW);
         j[u] = cp[(int64_t)(k + u) * kSliceW];
       }
     }
@@ -219,7 +220,7 @@ __device__ __forceinline__ void cand_entry(const DevMatrix &M, const DevState &S
     const uint32_t c = E.cs >> 2;
     const RowSum rs = S.rowsum[c];
     const double2 sd = S.side[c];
-    const double a = M.val[E.off];
+    const double a = ld_coef(M, E.off);
     const int32_t j = M.col[E.off];
     double L, U;
     float WU, WL;
@@ -260,7 +261,9 @@ constexpr int kRoundWarpsPerSM = 24;
 constexpr int kGroup = 4;         // slots per group in the activity loop
 
 // One slice of the round (warp-level: the 32 lanes are its 32 chunks).
-template <bool kMulti>
+// kVal8: the coefficients come from the int8 copy (converted when used, so
+// that the prefetched loads stay in flight).
+template <bool kMulti, bool kVal8>
 __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &S, int slice) {
   const Ctrl *ctrl = S.ctrl;
   const int lane = threadIdx.x & 31;
@@ -279,9 +282,8 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
     }
   }
   const int64_t sbase = M.slice_off[slice];
-  const double *svp = M.val + sbase;
   const int32_t *scp = M.col + sbase;
-  const double *vp = svp + lane;
+  const int64_t vo = sbase + lane;
   const int32_t *cp = scp + lane;
 
   // A side's activity is needed only by rows whose side is finite (Step 2
@@ -300,19 +302,28 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
   // before any is consumed, and the next group's values and columns are
   // fetched while this group's gathers are in flight; the last group's
   // missing slots are skipped (uniformly within a length-sorted slice)
-  double an[kGroup];
+  using Raw = typename std::conditional<kVal8, int, double>::type;
+  auto raw = [&](int64_t off) -> Raw {
+    if constexpr (kVal8) return (int)__ldcs(M.val8 + off);
+    else return __ldcs(M.val + off);
+  };
+  auto coef = [](Raw r) -> double {
+    if constexpr (kVal8) return small_int_to_double(r);
+    else return r;
+  };
+  Raw an[kGroup];
   int32_t jn[kGroup];
 #pragma unroll
   for (int u = 0; u < kGroup; ++u) {
-    an[u] = 1.0;
+    an[u] = (Raw)1;
     jn[u] = 0;
     if (u < len) {
-      an[u] = __ldcs(vp + (int64_t)u * kSliceW);
+      an[u] = raw(vo + (int64_t)u * kSliceW);
       jn[u] = __ldcs(cp + (int64_t)u * kSliceW);
     }
   }
   for (int k = 0; k < len; k += kGroup) {
-    double a[kGroup];
+    Raw a[kGroup];
     double L[kGroup], U[kGroup];
     float WU[kGroup], WL[kGroup];
     uint32_t fl[kGroup];
@@ -326,10 +337,10 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
     if (k + kGroup < len) {
 #pragma unroll
       for (int u = 0; u < kGroup; ++u) {
-        an[u] = 1.0;
+        an[u] = (Raw)1;
         jn[u] = 0;
         if (k + kGroup + u < len) {
-          an[u] = __ldcs(vp + (int64_t)(k + kGroup + u) * kSliceW);
+          an[u] = raw(vo + (int64_t)(k + kGroup + u) * kSliceW);
           jn[u] = __ldcs(cp + (int64_t)(k + kGroup + u) * kSliceW);
         }
       }
@@ -337,14 +348,15 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
 #pragma unroll
     for (int u = 0; u < kGroup; ++u) {
       if (k + u < len) {
-        bool pos = d_pos(a[u]);
-        float au = absup_fast(a[u]), ad = absdn_fast(a[u]);
+        const double av = coef(a[u]);
+        bool pos = d_pos(av);
+        float au = absup_fast(av), ad = absdn_fast(av);
         if (need_min) {
           double bmin = pos ? L[u] : U[u];
           bool imin = d_isinf(bmin);
           mininf += imin;
           if (imin) t.kinf_min = k + u;
-          minfin = fma(a[u], imin ? 0.0 : bmin, minfin);
+          minfin = fma(av, imin ? 0.0 : bmin, minfin);
           top2_add(screen_prod(au, ad, pos ? WU[u] : WL[u]), k + u, t.r1, t.r2, t.kr);
         }
         if (need_max) {
@@ -352,7 +364,7 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
           bool imax = d_isinf(bmax);
           maxinf += imax;
           if (imax) t.kinf_max = k + u;
-          maxfin = fma(a[u], imax ? 0.0 : bmax, maxfin);
+          maxfin = fma(av, imax ? 0.0 : bmax, maxfin);
           top2_add(screen_prod(au, ad, pos ? WL[u] : WU[u]), k + u, t.l1, t.l2, t.kl);
         }
       }
@@ -392,16 +404,16 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
   } else {
     rv.lhs = rv.rhs = 0.0;
   }
-  warp_enqueue(rv, t, mininf, maxinf, len, c, sbase, M.val, M.col, S);
+  warp_enqueue(rv, t, mininf, maxinf, len, c, sbase, M, M.col, S);
 }
 
-template <bool kMulti, int kRoundWarps>
+template <bool kMulti, int kRoundWarps, bool kVal8>
 __global__ void __launch_bounds__(kRoundWarps * 32, kRoundWarpsPerSM / kRoundWarps)
 k_round(DevMatrix M, DevState S) {
   if (S.ctrl->err) return;
   const int slice = blockIdx.x * kRoundWarps + (threadIdx.x >> 5);
   if (slice >= M.nslices) return;  // warp-uniform
-  round_slice<kMulti>(M, S, slice);
+  round_slice<kMulti, kVal8>(M, S, slice);
 }
 
 // ------------------------------------------------------------ k_combine --
@@ -546,7 +558,7 @@ __device__ __forceinline__ void cand_split_slice(const DevMatrix &M, const DevSt
     }
   }
   const int64_t sbase = M.slice_off[slice];
-  warp_enqueue(rv, t, cmin, cmax, len, c, sbase, M.val, M.col, S);
+  warp_enqueue(rv, t, cmin, cmax, len, c, sbase, M, M.col, S);
 }
 
 template <int kRoundWarps>
@@ -719,7 +731,10 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
   for (;;) {
-    for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false>(M, S, sl);
+    if (M.val8)
+      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, true>(M, S, sl);
+    else
+      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, false>(M, S, sl);
     if (!grid_sync(S)) return;
     if (M.nsplit_rows > 0) {
       for (int w = gw; w < M.nsplit_rows; w += nw) combine_row<false>(M, S, w);
@@ -858,7 +873,10 @@ cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t 
   int nb = (M.nslices + kRoundWarps - 1) / kRoundWarps;
   if (nb < 1) nb = 1;
   if (ev) cudaEventRecord(ev[0], st);
-  k_round<kMulti, kRoundWarps><<<nb, kRoundWarps * 32, 0, st>>>(M, S);
+  if (M.val8)
+    k_round<kMulti, kRoundWarps, true><<<nb, kRoundWarps * 32, 0, st>>>(M, S);
+  else
+    k_round<kMulti, kRoundWarps, false><<<nb, kRoundWarps * 32, 0, st>>>(M, S);
   if (ev) cudaEventRecord(ev[1], st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (M.nsplit_rows > 0) {

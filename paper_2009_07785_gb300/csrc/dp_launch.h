@@ -76,6 +76,7 @@ struct HostLayout {
   int64_t nnz = 0;
   int32_t nslices = 0, nslices_split = 0, nsplit_rows = 0;
   std::vector<double> val;
+  std::vector<int8_t> val8;  // empty unless every coefficient is an integer in [-127, 127]
   std::vector<int32_t> col;
   std::vector<int64_t> slice_off;
   std::vector<int32_t> slice_len;

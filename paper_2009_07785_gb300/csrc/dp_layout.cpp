@@ -164,6 +164,14 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     if (total >= (int64_t(1) << 32)) return DP_ERR_INVALID_ARG;
     out.val.assign((size_t)total, 0.0);
     out.col.assign((size_t)total, 0);
+    // lossless int8 copy of the values when every coefficient is a small
+    // integer (the round kernels then stream 1 byte per value, not 8)
+    bool small = true;
+    for (int64_t k = 0; k < nnz && small; ++k) {
+      const double a = val[k];
+      small = a == std::nearbyint(a) && std::fabs(a) <= 127.0;
+    }
+    if (small) out.val8.assign((size_t)total, 0);
     out.chunk_row.resize(nslots);
     out.chunk_len.resize(nslots);
     out.chunk_sidx.assign(nsplit_chunks, -1);
@@ -176,6 +184,7 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
       for (int32_t k = 0; k < ch.len; ++k) {
         out.val[(size_t)(base + (int64_t)k * kSliceW)] = val[ch.begin + k];
         out.col[(size_t)(base + (int64_t)k * kSliceW)] = col_idx[ch.begin + k];
+        if (small) out.val8[(size_t)(base + (int64_t)k * kSliceW)] = (int8_t)val[ch.begin + k];
       }
     }
   } catch (const std::bad_alloc &) {

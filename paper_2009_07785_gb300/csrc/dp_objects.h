@@ -32,6 +32,7 @@ struct dp_matrix {
   cudaGraphExec_t exec = nullptr;
   // batched nodes (allocated on the first dp_propagate_nodes call)
   struct BatchWs *batch = nullptr;
+  const int8_t *val8 = nullptr;  // int8 copy of the values (small integers only)
   // problem sets (dp_matrix_load_set): first row / variable of each problem
   int32_t ninst = 0;
   std::vector<int32_t> row_off, var_off;

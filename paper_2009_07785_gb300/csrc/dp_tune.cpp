@@ -18,12 +18,12 @@ extern "C" int dp_autotune(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                            const double *lhs, const double *rhs, const dp_params *params,
                            int32_t rounds, dp_tune_entry *entries, int32_t max_entries,
                            int32_t *count, dp_tune_entry *best) {
-  if (!ctx || !best || rounds < 1 || max_entries < 0 || (max_entries > 0 && !entries) ||
+  if (!ctx || !best || max_entries < 0 || (max_entries > 0 && !entries) ||
       (m > 0 && !row_ptr))
     return DP_ERR_INVALID_ARG;
   dp_params p;
   if (params) p = *params; else dp_params_default(&p);
-  p.max_rounds = rounds;
+  if (rounds > 0) p.max_rounds = rounds;  // else: to the fixed point (or the cap)
   // distinct layouts only: every chunk at least as long as the longest row
   // gives the layout of the shortest such chunk
   int64_t maxlen = 0;
@@ -45,6 +45,7 @@ extern "C" int dp_autotune(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
       rc = dp_matrix_load(ctx, m, n, nnz, row_ptr, col_idx, val, chunk, &mat);
     }
     if (rc) return rc;
+    dp_matrix_set_compression(mat, 0, nullptr);  // the binary64 values (the default layout)
     for (int32_t w : shapes) {
       rc = dp_matrix_set_launch(mat, w);
       if (rc) break;
@@ -52,7 +53,7 @@ extern "C" int dp_autotune(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
       float ms[5];
       int32_t launches[5];
       double best_us = -1.0;
-      for (int rep = 0; rep < 3 && rc >= 0; ++rep) {  // first call warms up
+      for (int rep = 0; rep < 4 && rc >= 0; ++rep) {  // first call warms up
         rc = dp_propagate_hostloop(ctx, mat, lb, ub, vartype, lhs, rhs, &p, out_lb.data(),
                                    out_ub.data(), &inf, &rr, ms, launches);
         if (rc < 0 || rep == 0) continue;

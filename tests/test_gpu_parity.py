@@ -238,3 +238,29 @@ def test_persistent_loop_large_scaled_equals_graph(gpu):
         rp = dp.dp_propagate_persistent(ctx, mat, *d)
         assert rp.rounds == rg.rounds and rp.infeasible == rg.infeasible
         assert np.array_equal(host(rp.lb), host(rg.lb)) and np.array_equal(host(rp.ub), host(rg.ub))
+
+
+def test_value_compression_lossless(gpu, orc):
+    """Small-integer coefficients can be read as int8 (off by default);
+    results are bit-identical with compression on and off, and equal the
+    oracle."""
+    dp, ctx = gpu
+    inst = synth.tiny()
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        b0 = gpu_full(dp, ctx, mat, inst)  # default: binary64 values
+        assert mat.set_compression(True)
+        a = gpu_full(dp, ctx, mat, inst)
+        assert np.array_equal(a[0], b0[0]) and np.array_equal(a[1], b0[1])
+        check_full(dp, ctx, mat, inst, orc, exact=True)
+        assert not mat.set_compression(False)
+        b = gpu_full(dp, ctx, mat, inst)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2].rounds == b[2].rounds
+    # every small integer value, both signs, through the kernels' conversion
+    rng = np.random.default_rng(3)
+    big = synth.small_random(rng, 400, 300, 30, coef=(1, 127))
+    with dp.Matrix(ctx, big.m, big.n, big.row_ptr, big.col, big.val, 16) as mat:
+        assert mat.set_compression(True)
+        replay(dp, ctx, mat, big, orc)
+    med = synth.medium(scale=0.01)  # fractional coefficients: no int8 copy
+    with dp.Matrix(ctx, med.m, med.n, med.row_ptr, med.col, med.val) as mat:
+        assert not mat.set_compression(True)
