@@ -232,68 +232,31 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
   return r;
 }
 
-// Candidates of one nonzero for one node (Eq. 3a/3b via Eq. 5a/5b, Step 3
-// rounding, the acceptance threshold), applied with order-preserving 64-bit
-// atomics to the node's next state kp = {lower key, upper key}.  Returns
-// whether this lane made the first improvement of the entry in this round
-// (the atomic saw the start-of-round key), which puts the entry on the
-// dirty list exactly once per side.
+// Candidates of one nonzero for one node from the sides that survived the
+// screen (side_candidate), applied with order-preserving 64-bit atomics to
+// the node's next state kp = {lower key, upper key}.  Returns whether this
+// lane made the first improvement of the entry in this round (the atomic saw
+// the start-of-round key), which puts the entry on the dirty list exactly
+// once per side.
 __device__ __forceinline__ bool bnnz_candidates(double a, bool isint, double L, double U,
                                                 unsigned sides, const RowView &rv,
                                                 const BParams &P, long long *kp) {
-  const bool pos = d_pos(a);
-  const double bmin = pos ? L : U;
-  const double bmax = pos ? U : L;
-  double lc = 0.0, uc = 0.0;
-  bool hl = false, hu = false;
-  if (sides & 1u) {
-    const double res = (rv.mininf == 0) ? fma(-a, bmin, rv.minfin) : rv.minfin;
-    if (d_isfinite(res)) {
-      const double c = (rv.rhs - res) / a;
-      if (pos) { uc = c; hu = true; } else { lc = c; hl = true; }
-    }
-  }
-  if (sides & 2u) {
-    const double res = (rv.maxinf == 0) ? fma(-a, bmax, rv.maxfin) : rv.maxfin;
-    if (d_isfinite(res)) {
-      const double c = (rv.lhs - res) / a;
-      if (pos) { lc = c; hl = true; } else { uc = c; hu = true; }
-    }
-  }
-  // rounding, the infinity threshold and the acceptance tests follow the
-  // binary64 formulas exactly; comparisons, floor/ceil and max(1, |x|) run
-  // on the integer pipe (see the helpers), the sums and products in binary64
-  if (hl) {
-    if (isint) lc = d_ceil_int(lc - P.eps_int);
-    if (!d_abs_lt(lc, P.inf_thr)) hl = false;
-  }
-  if (hu) {
-    if (isint) uc = d_floor_int(uc + P.eps_int);
-    if (!d_abs_lt(uc, P.inf_thr)) hu = false;
-  }
   bool first = false;
-  if (hl) {
-    bool acc;
-    if (d_is_neginf(L)) acc = true;
-    else if (isint) acc = cmp_key(lc) > cmp_key(L);
-    else acc = cmp_key(lc) > cmp_key(L + P.tau_rel * d_max1abs(L));
-    if (acc) {
-      const long long nk = key_of(lc), k0 = key_of(L);
-      const long long old = atomicMax(&kp[0], nk);
-      first |= (old == k0 && nk > old);
-    }
-  }
-  if (hu) {
-    bool acc;
-    if (d_is_posinf(U)) acc = true;
-    else if (isint) acc = cmp_key(uc) < cmp_key(U);
-    else acc = cmp_key(uc) < cmp_key(U - P.tau_rel * d_max1abs(U));
-    if (acc) {
-      const long long nk = key_of(uc), k0 = key_of(U);
+  auto apply = [&](const SideCand &c) {
+    if (!c.apply) return;
+    const long long nk = key_of(c.v);
+    if (c.upper) {
       const long long old = atomicMin(&kp[1], nk);
-      first |= (old == k0 && nk < old);
+      first |= (old == key_of(U) && nk < old);
+    } else {
+      const long long old = atomicMax(&kp[0], nk);
+      first |= (old == key_of(L) && nk > old);
     }
-  }
+  };
+  apply(side_candidate(a, L, U, isint, (sides & 1u) != 0u, rv, P.eps_int, P.tau_rel,
+                       P.inf_thr));
+  if (sides == 3u)
+    apply(side_candidate(a, L, U, isint, false, rv, P.eps_int, P.tau_rel, P.inf_thr));
   return first;
 }
 

@@ -262,6 +262,15 @@ __device__ __forceinline__ void set_flag(int32_t *f) {
   __threadfence();
 }
 
+// Sign change of a binary64 value on the integer pipe (exact).
+__device__ __forceinline__ double d_neg(double x) {
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  double r;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi ^ 0x80000000u));
+  return r;
+}
+
 // ------------------------------------------------------- per-row decisions --
 
 // What the candidate step needs to know about one row (kept in shared
@@ -315,6 +324,48 @@ __device__ __forceinline__ bool row_sides_eval(RowView &rv, float Tr, float Tl,
 __device__ __forceinline__ void row_sides(RowView &rv, float Tr, float Tl, double eps_feas,
                                           int32_t *infeasible_flag) {
   if (row_sides_eval(rv, Tr, Tl, eps_feas)) set_flag(infeasible_flag);
+}
+
+// One bound candidate of one nonzero from one side of its row (Eq. 3a/3b in
+// the residual form of Eq. 5a/5b, with the exactly-one-infinity rule of
+// Sec. 3.4), its integer rounding (Step 3), the infinity threshold and the
+// acceptance test against the start-of-round bound (Sec. 3.5).  The
+// right-hand side gives an upper candidate for a > 0 and a lower one for
+// a < 0; the left-hand side the reverse.  The steps are written once, for
+// upper candidates: a lower candidate c is processed as the upper candidate
+// -c of -x (ceil(c - eps) = -floor(-c + eps), and c > L + t(L) iff
+// -c < -L - t(-L), all exact under negation), so that a warp whose lanes mix
+// sides and signs issues one division, not one per case.
+struct SideCand {
+  double v;    // the candidate (rounded for integers)
+  bool upper;  // an upper bound candidate (else lower)
+  bool apply;  // it passes the threshold and the acceptance test
+};
+
+__device__ __forceinline__ SideCand side_candidate(double a, double L, double U, bool isint,
+                                                   bool use_rhs, const RowView &rv,
+                                                   double eps_int, double tau_rel,
+                                                   double inf_thr) {
+  SideCand c;
+  c.v = 0.0;
+  c.apply = false;
+  const bool pos = d_pos(a);
+  c.upper = use_rhs == pos;
+  const int32_t ninf = use_rhs ? rv.mininf : rv.maxinf;
+  const double fin = use_rhs ? rv.minfin : rv.maxfin;
+  const double bnd = c.upper ? L : U;  // this nonzero's term in that activity
+  const double res = (ninf == 0) ? fma(-a, bnd, fin) : fin;
+  if (!d_isfinite(res)) return c;
+  const double q = ((use_rhs ? rv.rhs : rv.lhs) - res) / a;
+  const double x = c.upper ? q : d_neg(q);
+  const double B = c.upper ? U : d_neg(L);
+  const double xr = isint ? d_floor_int(x + eps_int) : x;
+  if (!d_abs_lt(xr, inf_thr)) return c;
+  if (d_is_posinf(B)) c.apply = true;
+  else if (isint) c.apply = cmp_key(xr) < cmp_key(B);
+  else c.apply = cmp_key(xr) < cmp_key(B - tau_rel * d_max1abs(B));
+  c.v = c.upper ? xr : d_neg(xr);
+  return c;
 }
 
 // Which sides of one nonzero survive the screen (bit 0: right-hand side,

@@ -34,63 +34,25 @@
 
 namespace dp {
 
-// Bound candidates of one nonzero (Eq. 3a/3b in the residual form of
-// Eq. 5a/5b, with the exactly-one-infinity rule of Sec. 3.4), integer
-// rounding (Step 3), and the filtered atomic update (Sec. 3.5).  Candidates
-// are compared with the bounds at the start of the round (L, U) and applied
-// to the next state with order-preserving 64-bit atomics.
+// Bound candidates of one nonzero from the sides that survived the screen
+// (side_candidate), applied to the next state with order-preserving 64-bit
+// atomics.  Candidates are compared with the bounds at the start of the
+// round (L, U).
 __device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L, double U,
                                                uint32_t flags, unsigned sides,
                                                const RowView &rv, const Ctrl &prm,
                                                long long *keys, int32_t *changed) {
-  bool pos = d_pos(a);
-  double bmin = pos ? L : U;
-  double bmax = pos ? U : L;
-  double lc = 0.0, uc = 0.0;
-  bool hl = false, hu = false;
-  if (sides & 1u) {
-    double res = (rv.mininf == 0) ? fma(-a, bmin, rv.minfin) : rv.minfin;
-    if (d_isfinite(res)) {
-      double c = (rv.rhs - res) / a;
-      if (pos) { uc = c; hu = true; } else { lc = c; hl = true; }
-    }
-  }
-  if (sides & 2u) {
-    double res = (rv.maxinf == 0) ? fma(-a, bmax, rv.maxfin) : rv.maxfin;
-    if (d_isfinite(res)) {
-      double c = (rv.lhs - res) / a;
-      if (pos) { lc = c; hl = true; } else { uc = c; hu = true; }
-    }
-  }
-  bool isint = (flags & 1u) != 0u;
-  if (hl) {
-    if (isint) lc = ceil(lc - prm.eps_int);
-    if (!(fabs(lc) < prm.inf_thr)) hl = false;
-  }
-  if (hu) {
-    if (isint) uc = floor(uc + prm.eps_int);
-    if (!(fabs(uc) < prm.inf_thr)) hu = false;
-  }
-  if (hl) {
-    bool acc;
-    if (d_is_neginf(L)) acc = true;
-    else if (isint) acc = lc > L;
-    else acc = lc > L + prm.tau_rel * fmax(1.0, fabs(L));
-    if (acc) {
-      atomicMax(&keys[2 * (int64_t)j], key_of(lc));
-      *changed = 1;
-    }
-  }
-  if (hu) {
-    bool acc;
-    if (d_is_posinf(U)) acc = true;
-    else if (isint) acc = uc < U;
-    else acc = uc < U - prm.tau_rel * fmax(1.0, fabs(U));
-    if (acc) {
-      atomicMin(&keys[2 * (int64_t)j + 1], key_of(uc));
-      *changed = 1;
-    }
-  }
+  const bool isint = (flags & 1u) != 0u;
+  auto apply = [&](const SideCand &c) {
+    if (!c.apply) return;
+    if (c.upper) atomicMin(&keys[2 * (int64_t)j + 1], key_of(c.v));
+    else atomicMax(&keys[2 * (int64_t)j], key_of(c.v));
+    *changed = 1;
+  };
+  apply(side_candidate(a, L, U, isint, (sides & 1u) != 0u, rv, prm.eps_int, prm.tau_rel,
+                       prm.inf_thr));
+  if (sides == 3u)  // both sides: the left-hand one too
+    apply(side_candidate(a, L, U, isint, false, rv, prm.eps_int, prm.tau_rel, prm.inf_thr));
 }
 
 __device__ __forceinline__ void top2_add(float t, int k, float &t1, float &t2, int32_t &k1) {
