@@ -199,6 +199,26 @@ def dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, pg) -> float:
+    """The largest of every rank's x (the whole job takes as long as its
+    slowest rank).  pg: torch.distributed (NCCL: CUDA tensor; gloo: CPU), or
+    None for one process."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, ranks: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas: every rank processes the same workload)."""
+    return units_per_rank * ranks / seconds_max
+
+
 def cpu_oracle_rounds(inst, seconds):
     """Times oracle rounds from the initial bounds until `seconds` elapse or
     the fixed point; returns (rounds, elapsed)."""
@@ -561,18 +581,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
-    ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), pg)
     clk = clocks.stop() if clocks else None
 
-    units = inst.nnz * rounds * args.steps * ws
-    value = units / (ms / 1e3)
+    value = job_value(inst.nnz * rounds * args.steps, ws, ms / 1e3)
     per_round_us = ms * 1e3 / (args.steps * rounds)
     split = info["split_rows"] > 0
-    launches = args.steps * (2 + (4 if split else 2) * rounds)
+    # per step: prologue (2 kernels) and epilogue (1); per round: k_round,
+    # k_cand_queue, k_finish, plus k_combine and k_cand_split with split rows
+    launches = args.steps * (3 + (5 if split else 3) * rounds)
 
     # the same propagation with the loop in one persistent (cooperative) kernel
     persistent = None
@@ -643,15 +660,12 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(ke):
             re = dp.dp_propagate(ctx, mat, *h_in, lb_out=h_lb, ub_out=h_ub)
-        el = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([el], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, pg)
         assert re.rounds == rounds
         h2d = sum(int(a.numel() * a.element_size()) for a in h_in)
         d2h = 16 * inst.n + 64
-        e2e = {"value": inst.nnz * rounds * ke * ws / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_value(inst.nnz * rounds * ke, ws, el), "unit": UNIT,
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": el * 1e3 / ke}
 
     cpu = None
