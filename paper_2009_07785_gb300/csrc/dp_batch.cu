@@ -401,7 +401,20 @@ __global__ void __launch_bounds__(kThreads) k_bmark(DevMatrix M, BatchState S) {
         } else if (first) {
           m = make_uint4(kFull, kFull, kFull, kFull);
         } else {
-          for (int k = 0; k < len; ++k) {
+          // four elements' loads in flight at a time
+          int k = 0;
+          for (; k + 4 <= len; k += 4) {
+            int32_t j[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) j[u] = M.col[base + (int64_t)(k + u) * kSliceW];
+            uint4 w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              w[u] = *reinterpret_cast<const uint4 *>(chg + (int64_t)j[u] * P.Gs + gq);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) m = or4(m, w[u]);
+          }
+          for (; k < len; ++k) {
             const int32_t j = M.col[base + (int64_t)k * kSliceW];
             m = or4(m, *reinterpret_cast<const uint4 *>(chg + (int64_t)j * P.Gs + gq));
           }
@@ -555,15 +568,25 @@ __global__ void __launch_bounds__(kThreads) k_bcombine(DevMatrix M, BatchState S
     rv.minfin = rv.maxfin = 0.0;
     rv.mininf = rv.maxinf = 0;
     float tr = -f_inf(), tl = -f_inf();
-    for (int32_t q = q0; q < q1; ++q) {  // the row's pieces in order
-      const BPartial pt = S.part[(int64_t)M.split_cidx[q] * P.Bp + node];
+    auto add = [&](const BPartial &pt) {
       rv.minfin += pt.minfin;
       rv.maxfin += pt.maxfin;
       rv.mininf += pt.mininf;
       rv.maxinf += pt.maxinf;
       tr = fmaxf(tr, pt.tr);
       tl = fmaxf(tl, pt.tl);
+    };
+    // the row's pieces in order; four pieces' loads in flight at a time (a
+    // row of hundreds of pieces would otherwise pay one load latency each)
+    int32_t q = q0;
+    for (; q + 4 <= q1; q += 4) {
+      BPartial pt[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pt[u] = S.part[(int64_t)M.split_cidx[q + u] * P.Bp + node];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) add(pt[u]);
     }
+    for (; q < q1; ++q) add(S.part[(int64_t)M.split_cidx[q] * P.Bp + node]);
     rv.lhs = S.lhs[row];
     rv.rhs = S.rhs[row];
     rv.exact = (M.chunk_len[c0] & kExactFlag) ? 1 : 0;
