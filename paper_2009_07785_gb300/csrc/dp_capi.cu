@@ -285,6 +285,7 @@ int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row
   TRY(dev_alloc(mat, &S.rowsum, (size_t)H.nslices * dp::kSliceW));
   TRY(dev_alloc(mat, &S.side, (size_t)H.nslices * dp::kSliceW));
   TRY(dev_alloc(mat, &S.ctrl, 1));
+  TRY(dev_alloc(mat, &S.dirty, ((size_t)n + 31) / 32));  // dirty bitmap
   TRY(dev_alloc(mat, &S.bar, 2));
   TRY(dev_alloc(mat, &mat->vt_ws, (size_t)n));
   TRY(dev_alloc(mat, &mat->st_lb, (size_t)n));

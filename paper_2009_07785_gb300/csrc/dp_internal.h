@@ -135,6 +135,7 @@ struct DevState {
   Partial *part;        // [nslices_split*32]
   RowTot *rowtot;       // [nsplit_rows]
   Ctrl *ctrl;
+  uint32_t *dirty;      // [ceil(n/32)] bit j: x_j's next state changed this round
   unsigned *bar;        // [2] grid barrier of the persistent loop: arrivals, generation
   InstState I;          // problem sets only
 };

@@ -37,22 +37,30 @@ namespace dp {
 // Bound candidates of one nonzero from the sides that survived the screen
 // (side_candidate), applied to the next state with order-preserving 64-bit
 // atomics.  Candidates are compared with the bounds at the start of the
-// round (L, U).
+// round (L, U).  A variable that receives a candidate is marked in the
+// round's dirty bitmap; the atomics return nothing, so none of them waits
+// for its answer.
 __device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L, double U,
                                                uint32_t flags, unsigned sides,
                                                const RowView &rv, const Ctrl &prm,
-                                               long long *keys, int32_t *changed) {
+                                               long long *keys, uint32_t *dirty,
+                                               int32_t *changed) {
   const bool isint = (flags & 1u) != 0u;
+  bool any = false;
   auto apply = [&](const SideCand &c) {
     if (!c.apply) return;
     if (c.upper) atomicMin(&keys[2 * (int64_t)j + 1], key_of(c.v));
     else atomicMax(&keys[2 * (int64_t)j], key_of(c.v));
-    *changed = 1;
+    any = true;
   };
   apply(side_candidate(a, L, U, isint, (sides & 1u) != 0u, rv, prm.eps_int, prm.tau_rel,
                        prm.inf_thr));
   if (sides == 3u)  // both sides: the left-hand one too
     apply(side_candidate(a, L, U, isint, false, rv, prm.eps_int, prm.tau_rel, prm.inf_thr));
+  if (any) {
+    atomicOr(&dirty[j >> 5], 1u << (j & 31));
+    *changed = 1;
+  }
 }
 
 __device__ __forceinline__ void top2_add(float t, int k, float &t1, float &t2, int32_t &k1) {
@@ -199,7 +207,7 @@ __device__ __forceinline__ void cand_entry(const DevMatrix &M, const DevState &S
     rv.exact = 0;
     rv.act = 1;
     int32_t *changed = kMulti ? &S.I.changed[S.I.slot_inst[c]] : &S.ctrl->changed;
-    nnz_candidates(a, j, L, U, fl, E.cs & 3u, rv, prm, S.keys, changed);
+    nnz_candidates(a, j, L, U, fl, E.cs & 3u, rv, prm, S.keys, S.dirty, changed);
   }
 }
 
@@ -560,6 +568,20 @@ __device__ __forceinline__ void finish_var(const DevState &S, const uint8_t *var
   write_var(S.rec + j, L, U, vt, tau_dn, eps_dn);
 }
 
+// Commits the variables marked in one word of the dirty bitmap and clears
+// the word (warp-level, all 32 lanes; the word is warp-uniform).
+template <bool kMulti>
+__device__ __forceinline__ void finish_word(const DevState &S, const uint8_t *vartype,
+                                            int64_t w, double eps_feas, float tau_dn,
+                                            float eps_dn) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t bits = S.dirty[w];
+  if (bits == 0u) return;
+  if ((bits >> lane) & 1u) finish_var<kMulti>(S, vartype, w * 32 + lane, eps_feas, tau_dn, eps_dn);
+  __syncwarp();
+  if (lane == 0) S.dirty[w] = 0u;
+}
+
 // Ends a round (one block, all threads; after every variable is committed):
 // counts the round, resets the round's counters and returns whether to
 // continue.  For a problem set each problem counts its rounds and stops on
@@ -618,10 +640,12 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHand
   const int32_t err = ctrl->err;
   const double eps_feas = ctrl->eps_feas;
   const float tau_dn = f32_dn(ctrl->tau_rel), eps_dn = f32_dn(ctrl->eps_int);
-  if (!err)
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x)
-      finish_var<kMulti>(S, vartype, j, eps_feas, tau_dn, eps_dn);
+  if (!err) {  // only variables whose next state changed (the dirty bitmap)
+    const int64_t nwords = ((int64_t)n + 31) >> 5;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nwords;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5)
+      finish_word<kMulti>(S, vartype, w, eps_feas, tau_dn, eps_dn);
+  }
   __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -707,8 +731,8 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
     const int32_t cnt = ((volatile Ctrl *)S.ctrl)->qcount;
     for (int64_t e = gt; e < cnt; e += nt) cand_entry<false>(M, S, prm, (int32_t)e);
     if (!grid_sync(S)) return;
-    for (int64_t j = gt; j < M.n; j += nt)
-      finish_var<false>(S, vartype, j, prm.eps_feas, tau_dn, eps_dn);
+    for (int64_t w = gt >> 5; w < ((int64_t)M.n + 31) >> 5; w += nt >> 5)
+      finish_word<false>(S, vartype, w, prm.eps_feas, tau_dn, eps_dn);
     if (!grid_sync(S)) return;
     if (blockIdx.x == 0) decide_round<false>(S);
     if (!grid_sync(S)) return;
@@ -728,8 +752,12 @@ __global__ void k_prologue(DevState S, uint8_t *vt_ws, int32_t m, int32_t n,
   const float tau_dn = f32_dn(tau_rel), eps_dn = f32_dn(eps_int);
   const double pinf = __longlong_as_double(0x7FF0000000000000ll);
   int64_t total = (int64_t)(n > m ? n : m);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop (the block size and the stride are multiples of 32)
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < total;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    bool cross = false;
     if (i < n) {
       double L = lb[i], U = ub[i];
       uint8_t vt = vartype[i] ? 1 : 0;
@@ -748,7 +776,13 @@ __global__ void k_prologue(DevState S, uint8_t *vt_ws, int32_t m, int32_t n,
       reinterpret_cast<longlong2 *>(S.keys)[i] = make_longlong2(key_of(L), key_of(U));
       write_var(S.rec + i, L, U, vt, tau_dn, eps_dn);
       vt_ws[i] = vt;
+      cross = key_of(L) > key_of(U);
     }
+    // A round commits only the variables marked in the dirty bitmap; bounds
+    // that cross on input are marked for round 1, whose commit tests them.
+    // Writing whole words also clears what an aborted call left behind.
+    const unsigned cw = __ballot_sync(kFull, cross);
+    if (i0 < n && lane == 0) S.dirty[i0 >> 5] = cw;
     if (i < m) {
       double l = lhs[i], r = rhs[i];
       bool bad = d_isnan(l) || d_isnan(r) || l >= thr || r <= -thr;
@@ -857,7 +891,7 @@ cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t 
   k_cand_queue<kMulti><<<num_sms * 8, 256, 0, st>>>(M, S);
   if (ev) cudaEventRecord(ev[9], st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int nbf = grid_for(M.n, kFinishThreads, num_sms * 8);
+  int nbf = grid_for(M.n, kFinishThreads, num_sms * 4);
   if (ev) cudaEventRecord(ev[6], st);
   k_finish<kMulti><<<nbf, kFinishThreads, 0, st>>>(S, vt_ws, M.n, handle, use_cond);
   if (ev) cudaEventRecord(ev[7], st);
