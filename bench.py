@@ -20,6 +20,10 @@ value_compression: the same propagation reading the lossless int8 copy of
           instead of 12 (reported apart from the roofline fraction).
 persistent_loop: the same propagation with the round loop in one
           cooperative kernel (dp_propagate_persistent) instead of the graph.
+merge_path: the same propagation over the merge-path layout
+          (dp_matrix_load_merge) for several segment lengths: equal work
+          per thread instead of length-sorted slices; per-kernel times and
+          the largest difference to the sliced layout's bounds.
 batched_nodes: 256 branch-and-bound node bound vectors over the medium
           matrix (m=200k, ~2M nonzeros) propagated by one dp_propagate_nodes
           call, against the plain loop of one dp_propagate call per node.
@@ -55,6 +59,49 @@ UNIT = "nnz/s"
 PEAK_FALLBACK_GBS = 6800.0
 
 
+def merge_bench(dp, ctx, stream, inst, d_in, rounds, ref_lb, ref_ub, sliced_ms, steps,
+                ipts=(16, 32, 64, 128, 256)):
+    """The headline propagation over the merge-path layout, one entry per
+    segment length; `ref_lb/ref_ub` are the sliced layout's bounds."""
+    import torch
+
+    entries = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d_lb, d_ub = torch.empty_like(ref_lb), torch.empty_like(ref_ub)
+    for ipt in ipts:
+        with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, lhs=inst.lhs,
+                       rhs=inst.rhs, merge_ipt=ipt) as mm:
+            split = mm.info()["split_rows"]
+            for _ in range(2):
+                r = dp.dp_propagate(ctx, mm, *d_in, lb_out=d_lb, ub_out=d_ub)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                r = dp.dp_propagate(ctx, mm, *d_in, lb_out=d_lb, ub_out=d_ub)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mms = e0.elapsed_time(e1) / steps
+            assert r.rounds == rounds and not r.infeasible
+            fin = torch.isfinite(ref_lb) & torch.isfinite(ref_ub)
+            same_inf = bool(torch.equal(torch.isfinite(d_lb), torch.isfinite(ref_lb)) and
+                            torch.equal(torch.isfinite(d_ub), torch.isfinite(ref_ub)))
+            rel = torch.maximum((d_lb - ref_lb).abs() / ref_lb.abs().clamp(min=1.0),
+                                (d_ub - ref_ub).abs() / ref_ub.abs().clamp(min=1.0))[fin]
+            hl = dp.dp_propagate_hostloop(ctx, mm, *d_in, lb_out=d_lb, ub_out=d_ub, timing=True)
+            kus = {k: round(hl.kernel_ms[i] / hl.kernel_launches[i] * 1e3, 2)
+                   for i, k in enumerate(("act", "fix", "rows", "cand_queue", "finish"))
+                   if hl.kernel_launches[i]}
+            entries.append({"items_per_thread": ipt, "ms_per_step": round(mms, 3),
+                            "value": inst.nnz * rounds / (mms * 1e-3), "split_rows": split,
+                            "kernel_us": kus, "same_infinite_bounds": same_inf,
+                            "max_rel_diff_vs_sliced": float(rel.max()) if rel.numel() else 0.0})
+    best = min(entries, key=lambda e: e["ms_per_step"])
+    return {"unit": UNIT, "steps": steps, "sliced_ms_per_step": round(sliced_ms, 3),
+            "best": {"items_per_thread": best["items_per_thread"], "value": best["value"],
+                     "ms_per_step": best["ms_per_step"]},
+            "entries": entries}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -71,6 +118,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-merge", action="store_true",
+                    help="skip the merge-path layout measurement")
     ap.add_argument("--no-persistent", action="store_true",
                     help="skip the persistent-kernel round loop measurement")
     ap.add_argument("--no-nodes", action="store_true",
@@ -121,7 +170,8 @@ def peaks():
 def kernel_source_sha():
     """Hash of the sources that define k_round (kernel file + device helpers)."""
     csrc = ROOT / "paper_2009_07785_gb300" / "csrc"
-    data = b"".join((csrc / f).read_bytes() for f in ("dp_kernels.cu", "dp_device.cuh"))
+    data = b"".join((csrc / f).read_bytes()
+                    for f in ("dp_kernels.cu", "dp_device.cuh", "dp_round.cuh"))
     return hashlib.sha256(data).hexdigest()[:16]
 
 
@@ -630,6 +680,13 @@ def run_ours(args):
                        "stream_bytes_per_nonzero": 5,
                        "k_round_us": round(hc.kernel_ms[0] / max(hc.kernel_launches[0], 1) * 1e3, 2)}
 
+    # the merge-path layout, against the sliced layout's result
+    merge = None
+    if not args.no_merge:
+        step()
+        merge = merge_bench(dp, ctx, stream, inst, d_in, rounds, d_lb.clone(), d_ub.clone(),
+                            ms / args.steps, max(3, min(args.steps, 10)))
+
     # per-kernel CUDA-event timings with the host-driven loop (same kernels, same data)
     hl = dp.dp_propagate_hostloop(ctx, mat, *d_in, lb_out=d_lb, ub_out=d_ub)
     t_hl0 = time.perf_counter()
@@ -701,7 +758,7 @@ def run_ours(args):
                           "parallelism": f"replicas x{ws}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "value_compression": compression,
-               "persistent_loop": persistent, "batched_nodes": nodes,
+               "persistent_loop": persistent, "merge_path": merge, "batched_nodes": nodes,
                "batched_matrices": sets,
                "serving": serving}
         print(json.dumps(out))

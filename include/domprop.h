@@ -135,6 +135,28 @@ int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                          const double *rhs, dp_matrix **out);
 
 /*
+ * dp_matrix_load_sides with the merge-path layout instead of row chunks:
+ * rows (grouped by the finiteness of their sides when lhs/rhs are given,
+ * else in CSR order) stay in CSR, and the merged sequence of the m row
+ * ends and nnz nonzeros is cut into segments of `items_per_thread` items
+ * (4..4096), one per thread of the activity pass, so that every thread
+ * does the same work whatever the row lengths.  A row that lies within one
+ * segment is summed in CSR order (results bit-identical to the oracle's);
+ * a row that crosses segment boundaries is summed in pieces, combined in a
+ * fixed order by a second pass (results within the documented tolerance).
+ * This is the merge-based SpMV balancing that the paper's Conclusions and
+ * Outlook name as a direction beyond CSR-adaptive (Sec. 3.2).  Only
+ * dp_propagate and dp_propagate_hostloop accept such a matrix (the other
+ * entry points return DP_ERR_INVALID_ARG); dp_matrix_set_launch applies to
+ * its activity pass.  Limits as dp_matrix_load, and m + nnz must be below
+ * 2^30 * items_per_thread.  Returns as dp_matrix_load.
+ */
+int dp_matrix_load_merge(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col_idx,
+                         const double *val, int32_t items_per_thread,
+                         const double *lhs, const double *rhs, dp_matrix **out);
+
+/*
  * Loads `count` independent problems as one matrix: problem k has m[k]
  * rows, n[k] variables and the CSR arrays row_ptr[k], col_idx[k], val[k]
  * (host, as in dp_matrix_load, columns local to the problem); lhs/rhs

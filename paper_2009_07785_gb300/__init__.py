@@ -30,8 +30,10 @@ DP_ERR_TIMEOUT = -6
 
 # exported symbols, in header order
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
-           "dp_matrix_load_sides", "dp_matrix_load_set", "dp_matrix_set_offsets",
-           "dp_matrix_set_launch", "dp_matrix_set_compression", "dp_autotune", "dp_matrix_free", "dp_matrix_info", "dp_propagate", "dp_propagate_hostloop",
+           "dp_matrix_load_sides", "dp_matrix_load_merge", "dp_matrix_load_set",
+           "dp_matrix_set_offsets", "dp_matrix_set_launch", "dp_matrix_set_compression",
+           "dp_autotune", "dp_matrix_free", "dp_matrix_info", "dp_propagate",
+           "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes", "dp_propagate_set",
            "dp_propagate_persistent",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
@@ -91,6 +93,8 @@ def lib() -> C.CDLL:
     L.dp_matrix_load.restype = C.c_int
     L.dp_matrix_load_sides.argtypes = [vp, i32, i32, i64, vp, vp, vp, i32, vp, vp, C.POINTER(vp)]
     L.dp_matrix_load_sides.restype = C.c_int
+    L.dp_matrix_load_merge.argtypes = [vp, i32, i32, i64, vp, vp, vp, i32, vp, vp, C.POINTER(vp)]
+    L.dp_matrix_load_merge.restype = C.c_int
     L.dp_matrix_load_set.argtypes = [vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, C.POINTER(vp)]
     L.dp_matrix_load_set.restype = C.c_int
     L.dp_matrix_set_offsets.argtypes = [vp, C.POINTER(i32), vp, vp]
@@ -225,15 +229,26 @@ class Matrix:
     """A dp_matrix: a CSR constraint matrix resident on the GPU."""
 
     def __init__(self, ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int = 0,
-                 lhs=None, rhs=None):
+                 lhs=None, rhs=None, merge_ipt: int | None = None):
         """lhs/rhs (optional, host): the row sides known at load time, used
-        only to order rows by side pattern (dp_matrix_load_sides)."""
+        only to order rows by side pattern (dp_matrix_load_sides).  With
+        merge_ipt > 0 the matrix gets the merge-path layout with that many
+        items per thread (dp_matrix_load_merge; `chunk` is then unused)."""
         row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
         val = np.ascontiguousarray(val, dtype=np.float64)
         h = C.c_void_p()
         nnz = int(row_ptr[-1]) if m > 0 else 0
-        if lhs is None and rhs is None:
+        if merge_ipt is not None:
+            if lhs is not None:
+                lhs = np.ascontiguousarray(lhs, dtype=np.float64)
+                rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+            _check(lib().dp_matrix_load_merge(ctx.handle, int(m), int(n), nnz, _ptr(row_ptr),
+                                              _ptr(col_idx), _ptr(val), int(merge_ipt),
+                                              _ptr(lhs) if lhs is not None else None,
+                                              _ptr(rhs) if rhs is not None else None,
+                                              C.byref(h)), "dp_matrix_load_merge")
+        elif lhs is None and rhs is None:
             _check(lib().dp_matrix_load(ctx.handle, int(m), int(n), nnz, _ptr(row_ptr),
                                         _ptr(col_idx), _ptr(val), int(chunk), C.byref(h)),
                    "dp_matrix_load")
@@ -395,6 +410,12 @@ def dp_matrix_load(ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: i
 def dp_matrix_load_sides(ctx: Context, m: int, n: int, row_ptr, col_idx, val, chunk: int,
                          lhs, rhs) -> Matrix:
     return Matrix(ctx, m, n, row_ptr, col_idx, val, chunk, lhs, rhs)
+
+
+def dp_matrix_load_merge(ctx: Context, m: int, n: int, row_ptr, col_idx, val,
+                         items_per_thread: int, lhs=None, rhs=None) -> Matrix:
+    return Matrix(ctx, m, n, row_ptr, col_idx, val, lhs=lhs, rhs=rhs,
+                  merge_ipt=items_per_thread)
 
 
 def dp_matrix_free(mat: Matrix) -> None:

@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
               "--cudart", "shared", "-I", str(ROOT / "include")]
 SOURCES = ["dp_kernels.cu", "dp_capi.cu", "dp_layout.cpp", "dp_noalloc.cu", "dp_batch.cu",
-           "dp_server.cpp", "dp_tune.cpp"]
+           "dp_merge.cu", "dp_server.cpp", "dp_tune.cpp"]
 
 
 def nvcc() -> str:

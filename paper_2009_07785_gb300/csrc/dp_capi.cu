@@ -224,16 +224,19 @@ int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
 namespace {
 
 // Loads a matrix; with row_off/var_off (count+1 offsets each) it is the
-// block-diagonal union of `count` independent problems.
+// block-diagonal union of `count` independent problems; with merge_ipt > 0
+// it gets the merge-path layout with that many items per segment.
 int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
               const int32_t *col_idx, const double *val, int32_t chunk, const double *lhs,
               const double *rhs, const std::vector<int32_t> *row_off,
-              const std::vector<int32_t> *var_off, dp_matrix **out) {
+              const std::vector<int32_t> *var_off, dp_matrix **out, int32_t merge_ipt = 0) {
   if (!ctx || !out) return DP_ERR_INVALID_ARG;
   *out = nullptr;
   if ((lhs == nullptr) != (rhs == nullptr)) return DP_ERR_INVALID_ARG;
   dp::HostLayout H;
-  int rc = dp::build_layout(m, n, nnz, row_ptr, col_idx, val, chunk, lhs, rhs, H);
+  int rc = merge_ipt > 0
+               ? dp::build_merge_layout(m, n, nnz, row_ptr, col_idx, val, merge_ipt, lhs, rhs, H)
+               : dp::build_layout(m, n, nnz, row_ptr, col_idx, val, chunk, lhs, rhs, H);
   if (rc) return rc;
   CUDA_TRY(cudaSetDevice(ctx->device));
   dp_matrix *mat = new (std::nothrow) dp_matrix();
@@ -249,6 +252,11 @@ int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row
   M.nslices_split = H.nslices_split;
   M.nsplit_rows = H.nsplit_rows;
   M.round_warps = 8;
+  M.layout = H.layout;
+  M.mp_ipt = H.mp_ipt;
+  M.mp_nseg = H.mp_nseg;
+  M.mp_nlong = H.mp_nlong;
+  M.mp_npiece = (int32_t)H.mp_piece.size();
   mat->padded = (int64_t)H.val.size();
 #define TRY(x)                 \
   do {                         \
@@ -272,13 +280,24 @@ int load_impl(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz, const int64_t *row
   TRY(upload(mat, H.split_row, &M.split_row, st));
   TRY(upload(mat, H.split_cbeg, &M.split_cbeg, st));
   TRY(upload(mat, H.split_cidx, &M.split_cidx, st));
+  TRY(upload(mat, H.mp_ptr, &M.mp_ptr, st));
+  TRY(upload(mat, H.mp_srow, &M.mp_srow, st));
+  TRY(upload(mat, H.mp_piece, &M.mp_piece, st));
   dp::DevState &S = mat->S;
   TRY(dev_alloc(mat, &S.rec, (size_t)n));
   TRY(dev_alloc(mat, &S.keys, 2 * (size_t)n));
   TRY(dev_alloc(mat, &S.lhs, (size_t)m));
   TRY(dev_alloc(mat, &S.rhs, (size_t)m));
-  TRY(dev_alloc(mat, &S.part, (size_t)H.nslices_split * dp::kSliceW));
-  TRY(dev_alloc(mat, &S.rowtot, (size_t)H.nsplit_rows));
+  if (H.layout == dp::kLayoutMerge) {
+    // pieces: head and carry of every segment; activities of every row
+    TRY(dev_alloc(mat, &S.part, 2 * (size_t)H.mp_nseg));
+    TRY(dev_alloc(mat, &S.rowact, (size_t)m));
+    TRY(dev_alloc(mat, &S.mp_need, ((size_t)H.mp_nseg + 31) / 32));
+    TRY(dev_alloc(mat, &S.rowtot, (size_t)H.mp_nlong));
+  } else {
+    TRY(dev_alloc(mat, &S.part, (size_t)H.nslices_split * dp::kSliceW));
+    TRY(dev_alloc(mat, &S.rowtot, (size_t)H.nsplit_rows));
+  }
   // candidate queue: at most one entry per slot and round, so it never
   // overflows; row sums are stored per chunk slot
   TRY(dev_alloc(mat, &S.queue, (size_t)mat->padded));
@@ -345,6 +364,18 @@ int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                          dp_matrix **out) {
   return load_impl(ctx, m, n, nnz, row_ptr, col_idx, val, chunk, lhs, rhs, nullptr, nullptr,
                    out);
+}
+
+int dp_matrix_load_merge(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col_idx, const double *val,
+                         int32_t items_per_thread, const double *lhs, const double *rhs,
+                         dp_matrix **out) {
+  if (items_per_thread < 4 || items_per_thread > 4096) {
+    if (out) *out = nullptr;
+    return DP_ERR_INVALID_ARG;
+  }
+  return load_impl(ctx, m, n, nnz, row_ptr, col_idx, val, 0, lhs, rhs, nullptr, nullptr, out,
+                   items_per_thread);
 }
 
 int dp_matrix_load_set(dp_ctx *ctx, int32_t count, const int32_t *m, const int32_t *n,
@@ -559,7 +590,7 @@ int dp_propagate_persistent(dp_ctx *ctx, const dp_matrix *cmat, const double *lb
   int rc = check_call(ctx, cmat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
                       infeasible, rounds, &p);
   if (rc) return rc;
-  if (cmat->ninst > 0) return DP_ERR_INVALID_ARG;
+  if (cmat->ninst > 0 || cmat->M.layout != dp::kLayoutEll) return DP_ERR_INVALID_ARG;
   int coop = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess ||
       !coop)
@@ -891,7 +922,7 @@ int nodes_call(dp_ctx *ctx, const dp_matrix *cmat, int32_t count, const double *
                int32_t *rounds, int32_t *status, bool hostloop, float *kernel_ms,
                int32_t *kernel_launches) {
   if (!ctx || !cmat || count < 0) return DP_ERR_INVALID_ARG;
-  if (cmat->ctx != ctx) return DP_ERR_INVALID_ARG;
+  if (cmat->ctx != ctx || cmat->M.layout != dp::kLayoutEll) return DP_ERR_INVALID_ARG;
   if (count == 0) return DP_OK;
   if (!infeasible || !rounds) return DP_ERR_INVALID_ARG;
   dp_matrix *mat = const_cast<dp_matrix *>(cmat);

@@ -10,6 +10,17 @@
 //   slice_off[s] + 32*k + t, so the 32 lanes read 32 consecutive values and
 //   32 consecutive column indices per slot.  Within a chunk the slots keep
 //   the row's CSR order.
+//
+// Merge-path layout (an alternative to the above; the paper's Conclusions
+// and Outlook name newer SpMV algorithms than CSR-adaptive as a direction
+// for computing activities): rows, grouped by side class, in
+// plain CSR; the sequence of m row ends and nnz nonzeros (merged in CSR
+// order) is cut into segments of `mp_ipt` items, one per thread, so every
+// thread does equal work whatever the row lengths.  A thread sums the
+// nonzeros of its segment sequentially row by row; a row that lies inside
+// one segment is summed exactly as the CSR order sums it, a row that
+// crosses segment boundaries ("split row") is summed in pieces that a
+// second pass combines in segment order.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -19,6 +30,8 @@ namespace dp {
 constexpr int kSliceW = 32;                 // chunks per slice (= warp width)
 constexpr int32_t kLenMask = 0x3FFFFFFF;    // chunk length bits
 constexpr int32_t kExactFlag = 1 << 30;     // row must skip the FP32 screen
+constexpr int32_t kLayoutEll = 0;           // sliced ELL over row chunks
+constexpr int32_t kLayoutMerge = 1;         // merge-path segments over CSR
 
 // Current bounds of one variable, as gathered by the round kernels: one
 // 32-byte record, fetched with a single 256-bit load per nonzero.
@@ -108,7 +121,24 @@ struct DevMatrix {
   const int32_t *split_row; // [nsplit_rows] row id of each split row
   const int32_t *split_cbeg;// [nsplit_rows+1] range of each split row in split_cidx
   const int32_t *split_cidx;// chunk slots of the split rows' pieces, row by row
+                            // (merge path: piece indices, 2t = head of
+                            // segment t, 2t+1 = its carry)
+  // merge-path layout only (layout == kLayoutMerge; val/col then hold the
+  // rows' CSR in side-class order, chunk_row maps that order to the
+  // caller's rows and chunk_len holds row length | kExactFlag)
+  int32_t layout;           // kLayoutEll or kLayoutMerge
+  int32_t mp_ipt;           // items (row ends + nonzeros) per segment
+  int32_t mp_nseg;          // segments (threads)
+  int32_t mp_pad;
+  const int32_t *mp_ptr;    // [m+1] CSR row offsets in side-class order
+  const int32_t *mp_srow;   // [mp_nseg+1] rows whose end precedes each segment
+  // rows longer than kMpLaneRow ("long rows"; chunk_sidx[p] = their index)
+  // are re-read for the screen by one warp per piece of <= kMpPiece nonzeros
+  int32_t mp_nlong, mp_npiece;
+  const int4 *mp_piece;     // [mp_npiece] {row, long index, CSR offset, length}
 };
+constexpr int32_t kMpLaneRow = 64;  // longest row whose screen one lane re-reads
+constexpr int32_t kMpPiece = 256;   // nonzeros per warp in the long-row re-read
 
 // Several independent problems in one matrix (their block-diagonal union:
 // each problem owns its rows and variables) with per-problem termination.
@@ -133,7 +163,9 @@ struct DevState {
   double *lhs, *rhs;    // [m] normalised sides
   double2 *side;        // [chunk slots] {lhs, rhs} of each chunk's row, in slot order
   Partial *part;        // [nslices_split*32]
-  RowTot *rowtot;       // [nsplit_rows]
+  RowTot *rowtot;       // [nsplit_rows] (merge path: [mp_nlong], long rows)
+  Partial *rowact;      // merge path: [m] activities of each row (side-class order)
+  uint32_t *mp_need;    // merge path: [ceil(mp_nseg/32)] activities a warp's rows need
   Ctrl *ctrl;
   uint32_t *dirty;      // [ceil(n/32)] bit j: x_j's next state changed this round
   unsigned *bar;        // [2] grid barrier of the persistent loop: arrivals, generation

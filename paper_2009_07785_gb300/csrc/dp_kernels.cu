@@ -9,14 +9,20 @@
 // round until k_finish clears the condition -- no host round trip):
 //   k_round      one warp per slice, one lane per chunk: activities of every
 //                chunk (Def. 1, Eq. 2a/2b, Sec. 3.4 infinity counts); for
-//                whole rows also Step 2, the screen, and the candidates
-//                (Eq. 3a/3b via Eq. 5a/5b) with filtered atomics (Sec. 3.5)
+//                whole rows also Step 2 and the binary32 screen, which
+//                queues the nonzeros whose candidates may be accepted
 //   k_combine    one warp per split row: sums the chunk partials in a fixed
 //                order, Step 2 and screen for the row
-//   k_cand_split one lane per chunk of an active split row: candidates
-//   k_finish     one thread per variable: decode the next state, crossing
-//                test (Sec. 1.1, remark after Step 3), write the records the
-//                next round gathers; the last block decides whether to loop
+//   k_cand_split one lane per chunk of an active split row: queueing
+//   k_cand_queue one thread per queued nonzero: the candidates (Eq. 3a/3b
+//                via Eq. 5a/5b) with filtered atomics (Sec. 3.5); marks the
+//                variables it updates in a dirty bitmap
+//   k_finish     one warp per bitmap word: for each marked variable, decode
+//                the next state, crossing test (Sec. 1.1, remark after
+//                Step 3), write the record the next round gathers; the last
+//                block decides whether to loop
+// (The merge-path layout replaces the first three by the kernels of
+// dp_merge.cu.)
 //
 // GB300 has little binary64 throughput (about 0.5 T lane-ops/s, the same for
 // any number of active lanes in a warp), so binary64 work is kept lane-dense:
@@ -29,6 +35,7 @@
 
 #include "dp_device.cuh"
 #include "dp_internal.h"
+#include "dp_round.cuh"
 #include "dp_launch.h"
 #include "../../include/domprop.h"
 
@@ -60,122 +67,6 @@ __device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L, do
   if (any) {
     atomicOr(&dirty[j >> 5], 1u << (j & 31));
     *changed = 1;
-  }
-}
-
-__device__ __forceinline__ void top2_add(float t, int k, float &t1, float &t2, int32_t &k1) {
-  if (t > t1) {
-    t2 = t1;
-    t1 = t;
-    k1 = k;
-  } else if (t > t2) {
-    t2 = t;
-  }
-}
-
-__device__ __forceinline__ Top2 top2_init() {
-  Top2 t;
-  t.r1 = t.r2 = t.l1 = t.l2 = -f_inf();
-  t.kr = t.kl = 0;
-  t.kinf_min = t.kinf_max = 0;
-  return t;
-}
-
-// Queues nonzeros of the lanes' chunks whose candidates survive the screen.
-// Entries go to a global queue (warp-aggregated slots) and are evaluated by
-// k_cand_queue, one per thread, so the binary64 candidate formulas run
-// lane-dense across the whole GPU however few survivors a warp has.  When
-// the second-largest screen value of a side is below the threshold, only the
-// chunk's largest can survive and it is queued directly (no re-read);
-// otherwise the lane re-reads its chunk (values and columns from L2, records
-// through the same gather), four slots at a time.  All 32 lanes must call
-// this (warp collectives).
-__device__ __forceinline__ void warp_enqueue(const RowView &mine, const Top2 &t, int chunk_mininf,
-                                             int chunk_maxinf, int32_t mylen, int64_t chunk_slot,
-                                             int64_t slice_off_elems, const DevMatrix &M,
-                                             const int32_t *col, const DevState &S) {
-  const int lane = threadIdx.x & 31;
-  const bool act = mine.act != 0;
-  if (__ballot_sync(kFull, act) == 0u) return;
-  const unsigned lt = (1u << lane) - 1u;
-
-  bool wrote_sums = false;
-  auto push = [&](bool h, int k, unsigned sides) {
-    const unsigned pm = __ballot_sync(kFull, h);
-    if (pm == 0u) return;
-    const int leader = __ffs(pm) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&S.ctrl->qcount, __popc(pm));
-    base = __shfl_sync(kFull, base, leader);
-    if (!h) return;
-    if (!wrote_sums) {
-      RowSum rs;
-      rs.minfin = mine.minfin;
-      rs.maxfin = mine.maxfin;
-      rs.mininf = mine.mininf;
-      rs.maxinf = mine.maxinf;
-      S.rowsum[chunk_slot] = rs;
-      wrote_sums = true;
-    }
-    CandEntry e;
-    e.off = (uint32_t)(slice_off_elems + (int64_t)k * kSliceW + lane);
-    e.cs = ((uint32_t)chunk_slot << 2) | sides;
-    S.queue[base + __popc(pm & lt)] = e;
-  };
-
-  // Survivors can be named without re-reading the chunk unless a side has
-  // two screen values above its threshold (or the row skips the screen).
-  // With exactly one infinite contribution to a side's activity, only that
-  // nonzero gets a finite residual on that side (Sec. 3.4); its slot was
-  // recorded by the activity pass.
-  const bool full = act && (mine.exact || (mine.mininf == 0 && t.r2 > mine.thr_r) ||
-                            (mine.maxinf == 0 && t.l2 > mine.thr_l));
-  bool h1 = false, h2 = false;
-  int k1 = 0, k2 = 0;
-  if (act && !full) {
-    const bool fr = d_isfinite(mine.rhs), fl = d_isfinite(mine.lhs);
-    if (fr && mine.mininf == 0 && t.r1 > mine.thr_r) { h1 = true; k1 = t.kr; }
-    if (fr && mine.mininf == 1 && chunk_mininf > 0) { h1 = true; k1 = t.kinf_min; }
-    if (fl && mine.maxinf == 0 && t.l1 > mine.thr_l) { h2 = true; k2 = t.kl; }
-    if (fl && mine.maxinf == 1 && chunk_maxinf > 0) { h2 = true; k2 = t.kinf_max; }
-  }
-  const bool merge = h1 && h2 && k1 == k2;
-  push(h1, k1, merge ? 3u : 1u);
-  push(h2 && !merge, k2, 2u);
-
-  // full re-read of the chunk, four slots at a time
-  const int len = full ? mylen : 0;
-  int maxlen = len;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kFull, maxlen, o));
-  const int64_t vo = slice_off_elems + lane;
-  const int32_t *cp = col + slice_off_elems + lane;
-  for (int k = 0; k < maxlen; k += 4) {
-    double a[4];
-    int32_t j[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      a[u] = 1.0;
-      j[u] = 0;
-      if (k + u < len) {
-        a[u] = ld_coef(M, vo + (int64_t)(k + u) * kSliceW);
-        j[u] = cp[(int64_t)(k + u) * kSliceW];
-      }
-    }
-    unsigned sd[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      sd[u] = 0u;
-      if (k + u < len) {
-        double L, U;
-        float WU, WL;
-        uint32_t fl;
-        ld_rec(S.rec + j[u], L, U, WU, WL, fl);
-        sd[u] = nnz_sides(a[u], L, U, WU, WL, mine);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) push(sd[u] != 0u, k + u, sd[u]);
   }
 }
 
@@ -374,7 +265,7 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
   } else {
     rv.lhs = rv.rhs = 0.0;
   }
-  warp_enqueue(rv, t, mininf, maxinf, len, c, sbase, M, M.col, S);
+  warp_enqueue<kSliceW>(rv, t, mininf, maxinf, len, c, sbase + lane, M, M.col, S);
 }
 
 template <bool kMulti, int kRoundWarps, bool kVal8>
@@ -528,7 +419,7 @@ __device__ __forceinline__ void cand_split_slice(const DevMatrix &M, const DevSt
     }
   }
   const int64_t sbase = M.slice_off[slice];
-  warp_enqueue(rv, t, cmin, cmax, len, c, sbase, M, M.col, S);
+  warp_enqueue<kSliceW>(rv, t, cmin, cmax, len, c, sbase + lane, M, M.col, S);
 }
 
 template <int kRoundWarps>
@@ -852,6 +743,7 @@ cudaError_t launch_prologue(const DevMatrix &M, const DevState &S, uint8_t *vt_w
         M, S, lhs, rhs, thr);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && M.layout == kLayoutMerge) e = launch_merge_prologue(M, S, st);
   return e;
 }
 
@@ -861,10 +753,11 @@ cudaError_t launch_epilogue(const DevState &S, int32_t n, double *lb_out, double
   return cudaGetLastError();
 }
 
+// The sliced-ELL part of a round: activities, split rows, Step 2 and the
+// screen (events ev[0..5] as in launch_round_kernels).
 template <bool kMulti, int kRoundWarps>
-cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
-                           cudaGraphConditionalHandle handle, int use_cond, int num_sms,
-                           cudaStream_t st, cudaEvent_t *ev) {
+cudaError_t launch_ell_front(const DevMatrix &M, const DevState &S, cudaStream_t st,
+                             cudaEvent_t *ev) {
   cudaError_t e;
   int nb = (M.nslices + kRoundWarps - 1) / kRoundWarps;
   if (nb < 1) nb = 1;
@@ -887,6 +780,16 @@ cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t 
     if (ev) cudaEventRecord(ev[5], st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+template <bool kMulti, int kRoundWarps>
+cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
+                           cudaGraphConditionalHandle handle, int use_cond, int num_sms,
+                           cudaStream_t st, cudaEvent_t *ev) {
+  cudaError_t e = M.layout == kLayoutMerge ? launch_merge_front(M, S, num_sms, st, ev)
+                                           : launch_ell_front<kMulti, kRoundWarps>(M, S, st, ev);
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[8], st);
   k_cand_queue<kMulti><<<num_sms * 8, 256, 0, st>>>(M, S);
   if (ev) cudaEventRecord(ev[9], st);

@@ -70,11 +70,26 @@ cudaError_t launch_slots_extract(const DevMatrix &M, const BatchState &S, int32_
                                  const int32_t *slots, int32_t count, double *out,
                                  int num_sms, cudaStream_t st);
 
+// Merge-path layout (dp_merge.cu): the activity pass over the segments,
+// the combination of split rows and the per-row pass that runs Step 2 and
+// queues the nonzeros that survive the screen (with the warp-level re-read
+// of long rows).  With `ev`, the three are bracketed by ev[0..1], ev[2..3]
+// and ev[4..5].
+cudaError_t launch_merge_front(const DevMatrix &M, const DevState &S, int num_sms,
+                               cudaStream_t st, cudaEvent_t *ev);
+// Per call (after the sides are written): the activities each warp of the
+// activity pass needs.
+cudaError_t launch_merge_prologue(const DevMatrix &M, const DevState &S, cudaStream_t st);
+
 // Host image of the device layout described in dp_internal.h.
 struct HostLayout {
   int32_t m = 0, n = 0;
   int64_t nnz = 0;
   int32_t nslices = 0, nslices_split = 0, nsplit_rows = 0;
+  int32_t layout = kLayoutEll;
+  int32_t mp_ipt = 0, mp_nseg = 0, mp_nlong = 0;
+  std::vector<int32_t> mp_ptr, mp_srow;
+  std::vector<int4> mp_piece;
   std::vector<double> val;
   std::vector<int8_t> val8;  // empty unless every coefficient is an integer in [-127, 127]
   std::vector<int32_t> col;
@@ -91,5 +106,11 @@ struct HostLayout {
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
                  const int32_t *col_idx, const double *val, int32_t chunk,
                  const double *lhs_hint, const double *rhs_hint, HostLayout &out);
+
+// The same for the merge-path layout with `ipt` items per segment
+// (4..4096).
+int build_merge_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                       const int32_t *col_idx, const double *val, int32_t ipt,
+                       const double *lhs_hint, const double *rhs_hint, HostLayout &out);
 
 }  // namespace dp

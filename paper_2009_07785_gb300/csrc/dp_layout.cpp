@@ -46,14 +46,14 @@ int side_class(const double *lhs, const double *rhs, int32_t i) {
 }
 }  // namespace
 
-int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
-                 const int32_t *col_idx, const double *val, int32_t chunk,
-                 const double *lhs_hint, const double *rhs_hint, HostLayout &out) {
+namespace {
+// Checks a host CSR matrix: offsets from 0 to nnz, non-decreasing; columns
+// in range; finite nonzero coefficients.
+int validate_csr(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                 const int32_t *col_idx, const double *val) {
   if (m < 0 || n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return DP_ERR_INVALID_ARG;
   if (m > 0 && !row_ptr) return DP_ERR_INVALID_ARG;
   if (nnz > 0 && (!col_idx || !val)) return DP_ERR_INVALID_ARG;
-  if (chunk == 0) chunk = 256;
-  if (chunk < 8 || chunk > 4096) return DP_ERR_INVALID_ARG;
   if (m > 0) {
     if (row_ptr[0] != 0 || row_ptr[m] != nnz) return DP_ERR_BAD_CSR;
     for (int32_t i = 0; i < m; ++i)
@@ -66,6 +66,17 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     double a = val[k];
     if (!std::isfinite(a) || a == 0.0) return DP_ERR_BAD_CSR;
   }
+  return DP_OK;
+}
+}  // namespace
+
+int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                 const int32_t *col_idx, const double *val, int32_t chunk,
+                 const double *lhs_hint, const double *rhs_hint, HostLayout &out) {
+  if (chunk == 0) chunk = 256;
+  if (chunk < 8 || chunk > 4096) return DP_ERR_INVALID_ARG;
+  int rc = validate_csr(m, n, nnz, row_ptr, col_idx, val);
+  if (rc) return rc;
 
   try {
     out = HostLayout();
@@ -186,6 +197,105 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
         out.col[(size_t)(base + (int64_t)k * kSliceW)] = col_idx[ch.begin + k];
         if (small) out.val8[(size_t)(base + (int64_t)k * kSliceW)] = (int8_t)val[ch.begin + k];
       }
+    }
+  } catch (const std::bad_alloc &) {
+    return DP_ERR_OOM;
+  }
+  return DP_OK;
+}
+
+// Merge-path layout (dp_internal.h): rows in side-class order (stable), the
+// merged sequence of row ends and nonzeros cut into segments of `ipt`
+// items, the first row of each segment, and the split rows with their
+// pieces.  In the merged sequence the first nonzero of row p (side-class
+// order) is item p + ptr[p] and its row end is item p + ptr[p+1]; a row is
+// split when these fall in different segments ta < tb, and its pieces are
+// the carry of ta, the carries of the segments in between (which hold
+// nothing but nonzeros of the row) and the head of tb.
+int build_merge_layout(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                       const int32_t *col_idx, const double *val, int32_t ipt,
+                       const double *lhs_hint, const double *rhs_hint, HostLayout &out) {
+  if (ipt < 4 || ipt > 4096) return DP_ERR_INVALID_ARG;
+  int rc = validate_csr(m, n, nnz, row_ptr, col_idx, val);
+  if (rc) return rc;
+  const int64_t total = (int64_t)m + nnz;
+  const int64_t nseg = (total + ipt - 1) / ipt;
+  // piece indices (2 per segment) and row offsets are 32-bit
+  if (2 * nseg >= (int64_t(1) << 31)) return DP_ERR_INVALID_ARG;
+  try {
+    out = HostLayout();
+    out.m = m;
+    out.n = n;
+    out.nnz = nnz;
+    out.layout = kLayoutMerge;
+    out.mp_ipt = ipt;
+    out.mp_nseg = (int32_t)nseg;
+    out.nslices = (m + kSliceW - 1) / kSliceW;
+    // queue entries pack the row in 30 bits
+    if ((int64_t)out.nslices * kSliceW >= (int64_t(1) << 30)) return DP_ERR_INVALID_ARG;
+    // rows by side class, stable (no hints: CSR order)
+    std::vector<int32_t> perm((size_t)m);
+    {
+      int64_t cnt[5] = {0, 0, 0, 0, 0};
+      for (int32_t i = 0; i < m; ++i) cnt[side_class(lhs_hint, rhs_hint, i) + 1]++;
+      for (int c = 1; c < 5; ++c) cnt[c] += cnt[c - 1];
+      for (int32_t i = 0; i < m; ++i) perm[(size_t)cnt[side_class(lhs_hint, rhs_hint, i)]++] = i;
+    }
+    const size_t nslots = (size_t)out.nslices * kSliceW;
+    out.chunk_row.assign(nslots > 0 ? nslots : 0, -1);
+    out.chunk_len.assign(nslots > 0 ? nslots : 0, 0);
+    out.mp_ptr.assign((size_t)m + 1, 0);
+    out.val.resize((size_t)nnz);
+    out.col.resize((size_t)nnz);
+    int64_t at = 0;
+    for (int32_t p = 0; p < m; ++p) {
+      const int32_t i = perm[(size_t)p];
+      int32_t flag = 0;
+      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k, ++at) {
+        out.val[(size_t)at] = val[k];
+        out.col[(size_t)at] = col_idx[k];
+        if (!coef_screenable(val[k])) flag = kExactFlag;
+      }
+      out.mp_ptr[(size_t)p + 1] = (int32_t)at;
+      out.chunk_row[(size_t)p] = i;
+      out.chunk_len[(size_t)p] = (int32_t)(row_ptr[i + 1] - row_ptr[i]) | flag;
+    }
+    // rows whose end precedes each segment's first item (a walk of the
+    // merged sequence: a nonzero k of row p comes before p's row end)
+    out.mp_srow.assign((size_t)nseg + 1, m);
+    {
+      int32_t p = 0;
+      int64_t k = 0;
+      for (int64_t t = 0; t <= nseg; ++t) {
+        const int64_t d = t * ipt < total ? t * ipt : total;
+        while (p + k < d) {
+          if (p < m && k < out.mp_ptr[(size_t)p + 1]) ++k;
+          else ++p;
+        }
+        out.mp_srow[(size_t)t] = p;
+      }
+    }
+    // split rows and their pieces
+    out.split_cbeg.push_back(0);
+    for (int32_t p = 0; p < m; ++p) {
+      const int64_t ta = ((int64_t)p + out.mp_ptr[(size_t)p]) / ipt;
+      const int64_t tb = ((int64_t)p + out.mp_ptr[(size_t)p + 1]) / ipt;
+      if (ta == tb) continue;
+      out.split_row.push_back(p);
+      for (int64_t t = ta; t < tb; ++t) out.split_cidx.push_back((int32_t)(2 * t + 1));
+      out.split_cidx.push_back((int32_t)(2 * tb));
+      out.split_cbeg.push_back((int32_t)out.split_cidx.size());
+    }
+    out.nsplit_rows = (int32_t)out.split_row.size();
+    // long rows: their screen re-read is cut into pieces, one warp each
+    out.chunk_sidx.assign(nslots, -1);
+    for (int32_t p = 0; p < m; ++p) {
+      const int32_t b = out.mp_ptr[(size_t)p], len = out.mp_ptr[(size_t)p + 1] - b;
+      if (len <= kMpLaneRow) continue;
+      out.chunk_sidx[(size_t)p] = out.mp_nlong;
+      for (int32_t o = 0; o < len; o += kMpPiece)
+        out.mp_piece.push_back(make_int4(p, out.mp_nlong, b + o, len - o < kMpPiece ? len - o : kMpPiece));
+      ++out.mp_nlong;
     }
   } catch (const std::bad_alloc &) {
     return DP_ERR_OOM;

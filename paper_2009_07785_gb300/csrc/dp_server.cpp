@@ -501,6 +501,7 @@ int dp_server_create(dp_ctx *ctx, const dp_server_config *cfg, dp_server **out) 
 int dp_server_add_matrix(dp_server *s, const dp_matrix *mat, const uint8_t *vartype,
                          const double *lhs, const double *rhs, int32_t *matrix_id) {
   if (!s || !mat || !matrix_id || mat->ctx != s->ctx) return DP_ERR_INVALID_ARG;
+  if (mat->M.layout != dp::kLayoutEll) return DP_ERR_INVALID_ARG;
   const int32_t m = mat->M.m, n = mat->M.n;
   if ((n > 0 && !vartype) || (m > 0 && (!lhs || !rhs))) return DP_ERR_INVALID_ARG;
   if ((int64_t)n * s->Bp >= (int64_t(1) << 30) ||

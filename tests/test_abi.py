@@ -100,3 +100,8 @@ def test_host_side_argument_checks(lib):
                          None, 0, None, best) == dp.DP_ERR_INVALID_ARG
     assert L.dp_propagate_set(None, None, None, None, None, None, None, None, None, None, None,
                               None, None) == dp.DP_ERR_INVALID_ARG
+    out = ctypes.c_void_p(1)
+    for ipt in (3, 16, 4097):  # null context, and item counts outside 4..4096
+        assert L.dp_matrix_load_merge(None, 0, 0, 0, None, None, None, ipt, None, None,
+                                      ctypes.byref(out)) == dp.DP_ERR_INVALID_ARG
+        assert out.value is None
