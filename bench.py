@@ -118,6 +118,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compression", action="store_true",
+                    help="skip the int8-value measurement")
     ap.add_argument("--no-merge", action="store_true",
                     help="skip the merge-path layout measurement")
     ap.add_argument("--no-persistent", action="store_true",
@@ -660,7 +662,7 @@ def run_ours(args):
 
     # lossless value compression (int8 coefficients), reported apart
     compression = None
-    if can_compress:
+    if can_compress and not args.no_compression:
         mat.set_compression(True)
         for _ in range(2):
             rc_ = dp.dp_propagate(ctx, mat, *d_in, lb_out=d_lb, ub_out=d_ub)
