@@ -129,6 +129,9 @@ def parse():
     ap.add_argument("--nodes-only", action="store_true",
                     help="run only the batched node measurement (profiling captures)")
     ap.add_argument("--nodes-count", type=int, default=256)
+    ap.add_argument("--nodes-chunk", type=int, default=0,
+                    help="row split length for both sides of the batched-node bench "
+                         "(default: each side's autotuner)")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving (continuous batching) measurement")
     ap.add_argument("--serving-only", action="store_true")
@@ -337,27 +340,48 @@ def run_reference(args):
     return 0
 
 
-def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3):
+def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3, chunk=0):
     """Batched branch-and-bound nodes (dp_propagate_nodes, one call for all
     nodes) against the plain loop (one dp_propagate call per node, the same
     kernels' single-instance path) on the medium matrix, device-resident
     inputs, CUDA events on the library's stream.  Two node sets: fixings at
     random in-domain values (the stated workload; most nodes are infeasible
     after round 1) and fixings at the feasible point's values (every node
-    runs to its fixed point)."""
+    runs to its fixed point).  Each side gets its own autotuned layout: the
+    batched-node autotuner on the first 64 feasible-point nodes, the
+    single-instance autotuner on the first of them."""
     import torch
     from paper_2009_07785_gb300 import synth
 
     inst = synth.medium()
-    mat = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val)
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    vt, lhs, rhs = dev(inst.vartype), dev(inst.lhs), dev(inst.rhs)
     seed = synth.seed_for(3, 0)
     sets = {"random_values": synth.node_bounds(inst, count, seed=seed),
             "feasible_point_values": synth.node_bounds_at_point(inst, count, seed=seed)}
+    FL, FU = sets["feasible_point_values"]
+    if chunk:
+        tb = {"best": {"chunk": chunk}, "entries": []}
+        tp = {"best": {"chunk": chunk, "round_warps": 8}}
+    else:
+        tb = dp.dp_autotune_nodes(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
+                                  np.ascontiguousarray(FL[:64]), np.ascontiguousarray(FU[:64]),
+                                  inst.vartype, inst.lhs, inst.rhs)
+        tp = dp.dp_autotune(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
+                            np.ascontiguousarray(FL[0]), np.ascontiguousarray(FU[0]),
+                            inst.vartype, inst.lhs, inst.rhs, rounds=0)
+    torch.cuda.synchronize()
+    mat = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, tb["best"]["chunk"],
+                    lhs=inst.lhs, rhs=inst.rhs)
+    mat_p = dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
+                      tp["best"]["chunk"], lhs=inst.lhs, rhs=inst.rhs)
+    mat_p.set_launch(tp["best"]["round_warps"])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    vt, lhs, rhs = dev(inst.vartype), dev(inst.lhs), dev(inst.rhs)
     out = {"workload": f"{inst.name}: m={inst.m} n={inst.n} nnz={inst.nnz}, {count} node bound "
                        f"vectors fixing 1-5% of the integer variables (seed {seed})",
-           "count": count}
+           "count": count,
+           "batched_layout": {"chunk": tb["best"]["chunk"], "autotune": tb["entries"]},
+           "plain_layout": {"chunk": tp["best"]["chunk"],
+                            "round_warps": tp["best"]["round_warps"]}}
     ev = lambda: torch.cuda.Event(enable_timing=True)
     for name, (LB, UB) in sets.items():
         dLB, dUB = dev(LB), dev(UB)
@@ -376,12 +400,13 @@ def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3):
         o1 = torch.empty(inst.n, dtype=torch.float64, device="cuda")
         o2 = torch.empty_like(o1)
         for k in range(warmup):
-            dp.dp_propagate(ctx, mat, rows[k][0], rows[k][1], vt, lhs, rhs, lb_out=o1, ub_out=o2)
+            dp.dp_propagate(ctx, mat_p, rows[k][0], rows[k][1], vt, lhs, rhs, lb_out=o1,
+                            ub_out=o2)
         torch.cuda.synchronize()
         rounds_plain = []
         e0.record(stream)
         for k in range(count):
-            rp = dp.dp_propagate(ctx, mat, rows[k][0], rows[k][1], vt, lhs, rhs, lb_out=o1,
+            rp = dp.dp_propagate(ctx, mat_p, rows[k][0], rows[k][1], vt, lhs, rhs, lb_out=o1,
                                  ub_out=o2)
             rounds_plain.append(rp.rounds)
         e1.record(stream)
@@ -397,6 +422,7 @@ def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3):
                      "infeasible_nodes": int(r.infeasible.sum()),
                      "stage_ms": {k: round(v, 3) for k, v in zip(dp.NODE_STAGES, h.kernel_ms)}}
     mat.close()
+    mat_p.close()
     return out
 
 
@@ -505,12 +531,28 @@ def serving_bench(dp, ctx, rates=(1000, 5000, 10000, 20000, 50000), seconds=1.0,
     random pool matrix and one of its node bound vectors; requests are
     submitted at their arrival times (the submitting loop waits for each);
     latency = completion time - arrival time on the server's clock."""
+    import torch
+
     pool_insts, pool_nodes = serving_pool()
-    mats = [dp.Matrix(ctx, i.m, i.n, i.row_ptr, i.col, i.val) for i in pool_insts]
+    # each matrix's row split length from the batched-node autotuner on two
+    # of its node vectors (lanes at low load hold one or two nodes)
+    t0 = time.perf_counter()
+    chunks = []
+    for i, (lb, ub) in zip(pool_insts, pool_nodes):
+        tune = dp.dp_autotune_nodes(ctx, i.m, i.n, i.row_ptr, i.col, i.val,
+                                    np.ascontiguousarray(lb[:2]), np.ascontiguousarray(ub[:2]),
+                                    i.vartype, i.lhs, i.rhs)
+        chunks.append(tune["best"]["chunk"])
+    tune_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    mats = [dp.Matrix(ctx, i.m, i.n, i.row_ptr, i.col, i.val, c)
+            for i, c in zip(pool_insts, chunks)]
     out = {"pool": f"{len(mats)} matrices like the medium workload, nonzeros "
                    f"{min(i.nnz for i in pool_insts)}..{max(i.nnz for i in pool_insts)} "
                    f"(log-uniform), 16 node vectors each (1-5% integer fixings at x*)",
-           "slots_per_matrix": slots, "rates": []}
+           "slots_per_matrix": slots,
+           "row_split_lengths": {str(c): chunks.count(c) for c in sorted(set(chunks))},
+           "autotune_seconds": round(tune_s, 1), "rates": []}
     rng = np.random.default_rng(12345)
     for rate in rates:
         nreq = int(min(max_requests, rate * seconds))
@@ -576,7 +618,8 @@ def run_ours(args):
     if args.nodes_only:
         ctx = dp.Context(local, torch.cuda.current_stream())
         print(json.dumps({"batched_nodes": nodes_bench(dp, ctx, torch.cuda.current_stream(),
-                                                       count=args.nodes_count)}))
+                                                       count=args.nodes_count,
+                                                       chunk=args.nodes_chunk)}))
         ctx.close()
         return 0
     if args.sets_only:
@@ -736,7 +779,7 @@ def run_ours(args):
 
     nodes = None
     if ws == 1 and not args.no_nodes:
-        nodes = nodes_bench(dp, ctx, stream, count=args.nodes_count)
+        nodes = nodes_bench(dp, ctx, stream, count=args.nodes_count, chunk=args.nodes_chunk)
     sets = None
     if ws == 1 and not args.no_sets:
         sets = sets_bench(dp, ctx, stream)

@@ -230,6 +230,27 @@ int dp_autotune(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                 dp_tune_entry *entries, int32_t max_entries, int32_t *count,
                 dp_tune_entry *best);
 
+/*
+ * Autotuner of the batched-node path (dp_propagate_nodes): times the whole
+ * batched propagation of `nodes` node bound vectors (lb/ub [nodes*n],
+ * node-major, host or device, as in dp_propagate_nodes; nodes >= 1) for
+ * every row split length in {32, 64, 128, 256, 512} that gives a distinct
+ * layout, with the host-driven loop's CUDA-event stage times (the best of
+ * three timed calls).  In the batched kernels a warp walks a chunk for 32
+ * node lanes, so the split length bounds the serial chain of each work item:
+ * short pieces suit batches with few live nodes (a server's lanes), long
+ * ones batches of many nodes.  entries[].round_warps is 0 (the batched
+ * kernels have one launch shape); us_per_round is the batch's kernel time
+ * divided by its rounds.  Other arguments and results as dp_autotune.
+ */
+int dp_autotune_nodes(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
+                      const int64_t *row_ptr, const int32_t *col_idx,
+                      const double *val, int32_t nodes, const double *lb,
+                      const double *ub, const uint8_t *vartype, const double *lhs,
+                      const double *rhs, const dp_params *params,
+                      dp_tune_entry *entries, int32_t max_entries, int32_t *count,
+                      dp_tune_entry *best);
+
 /* Frees a matrix; NULL is a no-op. */
 void dp_matrix_free(dp_matrix *mat);
 

@@ -32,7 +32,7 @@ DP_ERR_TIMEOUT = -6
 SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_matrix_load",
            "dp_matrix_load_sides", "dp_matrix_load_merge", "dp_matrix_load_set",
            "dp_matrix_set_offsets", "dp_matrix_set_launch", "dp_matrix_set_compression",
-           "dp_autotune", "dp_matrix_free", "dp_matrix_info", "dp_propagate",
+           "dp_autotune", "dp_autotune_nodes", "dp_matrix_free", "dp_matrix_info", "dp_propagate",
            "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes", "dp_propagate_set",
            "dp_propagate_persistent",
@@ -107,6 +107,10 @@ def lib() -> C.CDLL:
                               C.POINTER(dp_params), i32, C.POINTER(dp_tune_entry), i32,
                               C.POINTER(i32), C.POINTER(dp_tune_entry)]
     L.dp_autotune.restype = C.c_int
+    L.dp_autotune_nodes.argtypes = [vp, i32, i32, i64, vp, vp, vp, i32, vp, vp, vp, vp, vp,
+                                    C.POINTER(dp_params), C.POINTER(dp_tune_entry), i32,
+                                    C.POINTER(i32), C.POINTER(dp_tune_entry)]
+    L.dp_autotune_nodes.restype = C.c_int
     L.dp_propagate_set.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp, vp,
                                    vp, vp]
     L.dp_propagate_set.restype = C.c_int
@@ -319,6 +323,27 @@ def dp_autotune(ctx: Context, m: int, n: int, row_ptr, col_idx, val, lb, ub, var
                              16, C.byref(cnt), C.byref(best)), "dp_autotune")
     conv = lambda e: {"chunk": e.chunk, "round_warps": e.round_warps,
                       "us_per_round": e.us_per_round}
+    return {"best": conv(best), "entries": [conv(ent[i]) for i in range(min(cnt.value, 16))]}
+
+
+def dp_autotune_nodes(ctx: Context, m: int, n: int, row_ptr, col_idx, val, lb, ub, vartype,
+                      lhs, rhs, params: dp_params | None = None) -> dict:
+    """Times the batched propagation of the node bound vectors lb, ub
+    ([nodes, n]) for each row split length; returns {"best": {...},
+    "entries": [...]} as dp_autotune (round_warps 0)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    nodes = int(lb.shape[0])
+    ent = (dp_tune_entry * 16)()
+    cnt = C.c_int32()
+    best = dp_tune_entry()
+    nnz = int(row_ptr[-1]) if m > 0 else 0
+    _check(lib().dp_autotune_nodes(ctx.handle, int(m), int(n), nnz, _ptr(row_ptr), _ptr(col_idx),
+                                   _ptr(val), nodes, _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs),
+                                   _ptr(rhs), C.byref(params) if params is not None else None,
+                                   ent, 16, C.byref(cnt), C.byref(best)), "dp_autotune_nodes")
+    conv = lambda e: {"chunk": e.chunk, "us_per_round": e.us_per_round}
     return {"best": conv(best), "entries": [conv(ent[i]) for i in range(min(cnt.value, 16))]}
 
 

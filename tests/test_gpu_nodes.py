@@ -203,3 +203,26 @@ def test_nodes_hostloop_matches_graph_loop(gpu):
         assert np.array_equal(h.lb.cpu().numpy(), lb) and np.array_equal(h.ub.cpu().numpy(), ub)
         assert np.array_equal(h.rounds, r.rounds) and np.array_equal(h.infeasible, r.infeasible)
         assert h.kernel_launches[0] == r.rounds.max() and all(t >= 0 for t in h.kernel_ms)
+
+
+def test_autotune_nodes_picks_a_measured_layout(gpu, orc):
+    """The batched-node autotuner times every distinct split length from 32
+    up and returns the fastest; nodes on its layout still match the oracle."""
+    dp, ctx = gpu
+    inst = synth.medium(scale=0.02)
+    LB, UB = synth.node_bounds_at_point(inst, 8, seed=4)
+    t = dp.dp_autotune_nodes(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, LB, UB,
+                             inst.vartype, inst.lhs, inst.rhs)
+    chunks = [e["chunk"] for e in t["entries"]]
+    us = [e["us_per_round"] for e in t["entries"]]
+    assert chunks[0] == 32 and chunks == sorted(set(chunks)) and len(chunks) >= 3
+    assert min(us) > 0 and t["best"]["us_per_round"] == min(us)
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
+                   t["best"]["chunk"]) as mat:
+        lb, ub, r = run_nodes(dp, ctx, mat, inst, LB, UB)
+    for k in range(LB.shape[0]):
+        o = orc.propagate(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, LB[k], UB[k],
+                          inst.vartype, inst.lhs, inst.rhs)
+        assert r.rounds[k] == o.rounds and r.infeasible[k] == o.infeasible, k
+        nbad, _, det = compare_bounds(lb[k], ub[k], o.lb, o.ub, inst.vartype)
+        assert nbad == 0, det
