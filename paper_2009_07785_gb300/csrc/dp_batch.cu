@@ -1060,8 +1060,17 @@ cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
   auto mark = [&](int k) {
     if (ev) cudaEventRecord(ev[k], st);
   };
+  // grid-stride over the chunks: at most the blocks resident at once
+  static int mark_blocks_per_sm = 0;
+  if (mark_blocks_per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bmark, kThreads, 0) != cudaSuccess ||
+        b < 1)
+      b = 4;
+    mark_blocks_per_sm = b;
+  }
   mark(0);
-  k_bmark<<<grid_for(nslots, kThreads, num_sms * 8), kThreads, 0, st>>>(M, S);
+  k_bmark<<<grid_for(nslots, kThreads, num_sms * mark_blocks_per_sm), kThreads, 0, st>>>(M, S);
   mark(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   mark(2);

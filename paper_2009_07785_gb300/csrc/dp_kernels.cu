@@ -17,10 +17,10 @@
 //   k_cand_queue one thread per queued nonzero: the candidates (Eq. 3a/3b
 //                via Eq. 5a/5b) with filtered atomics (Sec. 3.5); marks the
 //                variables it updates in a dirty bitmap
-//   k_finish     one warp per bitmap word: for each marked variable, decode
-//                the next state, crossing test (Sec. 1.1, remark after
-//                Step 3), write the record the next round gathers; the last
-//                block decides whether to loop
+//   k_finish     one warp per 8 bitmap words, per marked variable (the
+//                warp together): decode the next state, crossing test
+//                (Sec. 1.1, remark after Step 3), write the record the next
+//                round gathers; the last block decides whether to loop
 // (The merge-path layout replaces the first three by the kernels of
 // dp_merge.cu.)
 //
@@ -72,45 +72,76 @@ __device__ __forceinline__ void nnz_candidates(double a, int32_t j, double L, do
 
 // ---------------------------------------------------------- k_cand_queue --
 
-// Evaluates one queued nonzero (thread-level).
-template <bool kMulti>
-__device__ __forceinline__ void cand_entry(const DevMatrix &M, const DevState &S,
-                                           const Ctrl &prm, int32_t e) {
-  {
-    const CandEntry E = S.queue[e];
-    const uint32_t c = E.cs >> 2;
-    const RowSum rs = S.rowsum[c];
-    const double2 sd = S.side[c];
-    const double a = ld_coef(M, E.off);
-    const int32_t j = M.col[E.off];
-    double L, U;
-    float WU, WL;
-    uint32_t fl;
-    ld_rec(S.rec + j, L, U, WU, WL, fl);
+// One queued nonzero's operands: the entry, its row's sums and sides, its
+// coefficient and column, and the start-of-round record of its variable.
+struct QueuedNnz {
+  CandEntry E;
+  RowSum rs;
+  double2 sd;
+  double a;
+  int32_t j;
+  double L, U;
+  float WU, WL;
+  uint32_t fl;
+};
+
+// Evaluates kN queued nonzeros per thread (entries e0 + u*stride, u < kN,
+// those below cnt): every load of one dependence level is issued for all
+// of them before the next level, so kN chains are in flight at once.
+template <bool kMulti, int kN>
+__device__ __forceinline__ void cand_entries(const DevMatrix &M, const DevState &S,
+                                             const Ctrl &prm, int64_t e0, int64_t stride,
+                                             int32_t cnt) {
+  QueuedNnz q[kN];
+  bool ok[kN];
+#pragma unroll
+  for (int u = 0; u < kN; ++u) {
+    ok[u] = e0 + u * stride < cnt;
+    if (ok[u]) q[u].E = S.queue[e0 + u * stride];
+  }
+#pragma unroll
+  for (int u = 0; u < kN; ++u) {
+    if (!ok[u]) continue;
+    const uint32_t c = q[u].E.cs >> 2;
+    q[u].rs = S.rowsum[c];
+    q[u].sd = S.side[c];
+    q[u].a = ld_coef(M, q[u].E.off);
+    q[u].j = M.col[q[u].E.off];
+  }
+#pragma unroll
+  for (int u = 0; u < kN; ++u)
+    if (ok[u]) ld_rec(S.rec + q[u].j, q[u].L, q[u].U, q[u].WU, q[u].WL, q[u].fl);
+#pragma unroll
+  for (int u = 0; u < kN; ++u) {
+    if (!ok[u]) continue;
+    const uint32_t c = q[u].E.cs >> 2;
     RowView rv;
-    rv.minfin = rs.minfin;
-    rv.maxfin = rs.maxfin;
-    rv.mininf = rs.mininf;
-    rv.maxinf = rs.maxinf;
-    rv.lhs = sd.x;
-    rv.rhs = sd.y;
+    rv.minfin = q[u].rs.minfin;
+    rv.maxfin = q[u].rs.maxfin;
+    rv.mininf = q[u].rs.mininf;
+    rv.maxinf = q[u].rs.maxinf;
+    rv.lhs = q[u].sd.x;
+    rv.rhs = q[u].sd.y;
     rv.thr_r = rv.thr_l = f_inf();
     rv.exact = 0;
     rv.act = 1;
     int32_t *changed = kMulti ? &S.I.changed[S.I.slot_inst[c]] : &S.ctrl->changed;
-    nnz_candidates(a, j, L, U, fl, E.cs & 3u, rv, prm, S.keys, S.dirty, changed);
+    nnz_candidates(q[u].a, q[u].j, q[u].L, q[u].U, q[u].fl, q[u].E.cs & 3u, rv, prm, S.keys,
+                   S.dirty, changed);
   }
 }
 
-// Evaluates the queued nonzeros, one per thread (grid-stride).
+// Evaluates the queued nonzeros, one per thread and step (grid-stride; the
+// grid is sized to the blocks that fit on the GPU at once).
 template <bool kMulti>
 __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
   const Ctrl *ctrl = S.ctrl;
   if (ctrl->err) return;
   const int32_t cnt = ctrl->qcount;
   const Ctrl prm = *ctrl;
-  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x)
-    cand_entry<kMulti>(M, S, prm, e);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += stride)
+    cand_entries<kMulti, 1>(M, S, prm, e, stride, cnt);
 }
 
 // ------------------------------------------------------------- k_round --
@@ -459,18 +490,31 @@ __device__ __forceinline__ void finish_var(const DevState &S, const uint8_t *var
   write_var(S.rec + j, L, U, vt, tau_dn, eps_dn);
 }
 
-// Commits the variables marked in one word of the dirty bitmap and clears
-// the word (warp-level, all 32 lanes; the word is warp-uniform).
+constexpr int kFinishWords = 8;  // bitmap words per warp and step of k_finish
+
+// Commits the variables marked in words [w0, w0 + kFinishWords) of the
+// dirty bitmap and clears those words (warp-level, all 32 lanes): lanes
+// read one word each, then the warp commits the 32 variables of every
+// nonzero word together.
 template <bool kMulti>
-__device__ __forceinline__ void finish_word(const DevState &S, const uint8_t *vartype,
-                                            int64_t w, double eps_feas, float tau_dn,
-                                            float eps_dn) {
+__device__ __forceinline__ void finish_words(const DevState &S, const uint8_t *vartype,
+                                             int64_t w0, int64_t nwords, double eps_feas,
+                                             float tau_dn, float eps_dn) {
   const int lane = threadIdx.x & 31;
-  const uint32_t bits = S.dirty[w];
-  if (bits == 0u) return;
-  if ((bits >> lane) & 1u) finish_var<kMulti>(S, vartype, w * 32 + lane, eps_feas, tau_dn, eps_dn);
-  __syncwarp();
-  if (lane == 0) S.dirty[w] = 0u;
+  const int64_t w = w0 + lane;
+  uint32_t bits = 0u;
+  if (lane < kFinishWords && w < nwords) {
+    bits = S.dirty[w];
+    if (bits) S.dirty[w] = 0u;
+  }
+  unsigned todo = __ballot_sync(kFull, bits != 0u);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1u;
+    const uint32_t b = __shfl_sync(kFull, bits, src);
+    if ((b >> lane) & 1u)
+      finish_var<kMulti>(S, vartype, (w0 + src) * 32 + lane, eps_feas, tau_dn, eps_dn);
+  }
 }
 
 // Ends a round (one block, all threads; after every variable is committed):
@@ -533,9 +577,10 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHand
   const float tau_dn = f32_dn(ctrl->tau_rel), eps_dn = f32_dn(ctrl->eps_int);
   if (!err) {  // only variables whose next state changed (the dirty bitmap)
     const int64_t nwords = ((int64_t)n + 31) >> 5;
-    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nwords;
-         w += ((int64_t)gridDim.x * blockDim.x) >> 5)
-      finish_word<kMulti>(S, vartype, w, eps_feas, tau_dn, eps_dn);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = warp * kFinishWords; w0 < nwords; w0 += nwarps * kFinishWords)
+      finish_words<kMulti>(S, vartype, w0, nwords, eps_feas, tau_dn, eps_dn);
   }
   __shared__ int s_last;
   __syncthreads();
@@ -620,10 +665,11 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
       if (!grid_sync(S)) return;
     }
     const int32_t cnt = ((volatile Ctrl *)S.ctrl)->qcount;
-    for (int64_t e = gt; e < cnt; e += nt) cand_entry<false>(M, S, prm, (int32_t)e);
+    for (int64_t e = gt; e < cnt; e += nt) cand_entries<false, 1>(M, S, prm, e, nt, cnt);
     if (!grid_sync(S)) return;
-    for (int64_t w = gt >> 5; w < ((int64_t)M.n + 31) >> 5; w += nt >> 5)
-      finish_word<false>(S, vartype, w, prm.eps_feas, tau_dn, eps_dn);
+    for (int64_t w0 = (gt >> 5) * kFinishWords; w0 < ((int64_t)M.n + 31) >> 5;
+         w0 += (nt >> 5) * kFinishWords)
+      finish_words<false>(S, vartype, w0, ((int64_t)M.n + 31) >> 5, prm.eps_feas, tau_dn, eps_dn);
     if (!grid_sync(S)) return;
     if (blockIdx.x == 0) decide_round<false>(S);
     if (!grid_sync(S)) return;
@@ -790,11 +836,23 @@ cudaError_t launch_round_t(const DevMatrix &M, const DevState &S, const uint8_t 
   cudaError_t e = M.layout == kLayoutMerge ? launch_merge_front(M, S, num_sms, st, ev)
                                            : launch_ell_front<kMulti, kRoundWarps>(M, S, st, ev);
   if (e != cudaSuccess) return e;
+  // the queue kernel's grid: the blocks that are resident at once (a
+  // larger grid-stride grid would run its last blocks as a second wave)
+  static int queue_blocks_per_sm = 0;
+  if (queue_blocks_per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cand_queue<kMulti>, 256, 0) !=
+            cudaSuccess ||
+        b < 1)
+      b = 4;
+    queue_blocks_per_sm = b;
+  }
   if (ev) cudaEventRecord(ev[8], st);
-  k_cand_queue<kMulti><<<num_sms * 8, 256, 0, st>>>(M, S);
+  k_cand_queue<kMulti><<<num_sms * queue_blocks_per_sm, 256, 0, st>>>(M, S);
   if (ev) cudaEventRecord(ev[9], st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int nbf = grid_for(M.n, kFinishThreads, num_sms * 4);
+  // one warp per kFinishWords bitmap words
+  int nbf = grid_for(((int64_t)M.n + 31) / 32 * 32 / kFinishWords, kFinishThreads, num_sms * 6);
   if (ev) cudaEventRecord(ev[6], st);
   k_finish<kMulti><<<nbf, kFinishThreads, 0, st>>>(S, vt_ws, M.n, handle, use_cond);
   if (ev) cudaEventRecord(ev[7], st);
