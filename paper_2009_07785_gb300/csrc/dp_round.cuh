@@ -24,6 +24,23 @@ __device__ __forceinline__ Top2 top2_init() {
   return t;
 }
 
+// Reserves c (0..7) consecutive queue entries per lane with one atomic per
+// warp (all 32 lanes call): the lanes' offsets come from three ballots of
+// the bits of c, not from a shuffle scan.  Returns the lane's first entry
+// (meaningless when c = 0).
+__device__ __forceinline__ int warp_reserve(int c, int32_t *counter) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned b0 = __ballot_sync(kFull, c & 1), b1 = __ballot_sync(kFull, c & 2),
+                 b2 = __ballot_sync(kFull, c & 4);
+  const int total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+  if (total == 0) return 0;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(counter, total);
+  base = __shfl_sync(kFull, base, 0);
+  return base + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+}
+
 // Queues nonzeros of the lanes' chunks whose candidates survive the screen.
 // Entries go to a global queue (warp-aggregated slots) and are evaluated by
 // k_cand_queue, one per thread, so the binary64 candidate formulas run
@@ -42,33 +59,25 @@ __device__ __forceinline__ bool warp_enqueue(const RowView &mine, const Top2 &t,
                                              int chunk_maxinf, int32_t mylen, int64_t chunk_slot,
                                              int64_t elem0, const DevMatrix &M,
                                              const int32_t *col, const DevState &S) {
-  const int lane = threadIdx.x & 31;
   const bool act = mine.act != 0;
   if (__ballot_sync(kFull, act) == 0u) return false;
-  const unsigned lt = (1u << lane) - 1u;
 
   bool wrote_sums = false;
-  auto push = [&](bool h, int k, unsigned sides) {
-    const unsigned pm = __ballot_sync(kFull, h);
-    if (pm == 0u) return;
-    const int leader = __ffs(pm) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&S.ctrl->qcount, __popc(pm));
-    base = __shfl_sync(kFull, base, leader);
-    if (!h) return;
-    if (!wrote_sums) {
-      RowSum rs;
-      rs.minfin = mine.minfin;
-      rs.maxfin = mine.maxfin;
-      rs.mininf = mine.mininf;
-      rs.maxinf = mine.maxinf;
-      S.rowsum[chunk_slot] = rs;
-      wrote_sums = true;
-    }
+  auto sums = [&]() {  // the row's sums, once, before its first queued entry
+    if (wrote_sums) return;
+    RowSum rs;
+    rs.minfin = mine.minfin;
+    rs.maxfin = mine.maxfin;
+    rs.mininf = mine.mininf;
+    rs.maxinf = mine.maxinf;
+    S.rowsum[chunk_slot] = rs;
+    wrote_sums = true;
+  };
+  auto entry = [&](int k, unsigned sides) {
     CandEntry e;
     e.off = (uint32_t)(elem0 + (int64_t)k * kStride);
     e.cs = ((uint32_t)chunk_slot << 2) | sides;
-    S.queue[base + __popc(pm & lt)] = e;
+    return e;
   };
 
   // Survivors can be named without re-reading the chunk unless a side has
@@ -88,8 +97,13 @@ __device__ __forceinline__ bool warp_enqueue(const RowView &mine, const Top2 &t,
     if (fl && mine.maxinf == 1 && chunk_maxinf > 0) { h2 = true; k2 = t.kinf_max; }
   }
   const bool merge = h1 && h2 && k1 == k2;
-  push(h1, k1, merge ? 3u : 1u);
-  push(h2 && !merge, k2, 2u);
+  {
+    const bool q2 = h2 && !merge;
+    int pos = warp_reserve((h1 ? 1 : 0) + (q2 ? 1 : 0), &S.ctrl->qcount);
+    if (h1 || q2) sums();
+    if (h1) S.queue[pos++] = entry(k1, merge ? 3u : 1u);
+    if (q2) S.queue[pos] = entry(k2, 2u);
+  }
 
   // full re-read of the chunk, four slots at a time
   const int len = full ? mylen : 0;
@@ -122,8 +136,15 @@ __device__ __forceinline__ bool warp_enqueue(const RowView &mine, const Top2 &t,
         sd[u] = nnz_sides(a[u], L, U, WU, WL, mine);
       }
     }
+    // one reservation for the group's survivors of all lanes
+    int c = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) push(sd[u] != 0u, k + u, sd[u]);
+    for (int u = 0; u < 4; ++u) c += sd[u] != 0u;
+    int pos = warp_reserve(c, &S.ctrl->qcount);
+    if (c > 0) sums();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (sd[u] != 0u) S.queue[pos++] = entry(k + u, sd[u]);
   }
   return full;
 }
