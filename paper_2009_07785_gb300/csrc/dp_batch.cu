@@ -688,7 +688,7 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
         const double L = val_of_key(kk.x), U = val_of_key(kk.y);
         put_entry(S, e, L, U, S.vt[j] != 0, P.tau_dn, P.eps_dn);
         if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
-          const bool cross = S.vt[j] ? (L > U) : (L > U + P.eps_feas * fmax(1.0, fabs(U)));
+          const bool cross = S.vt[j] ? (L > U) : (L > U + P.eps_feas * d_max1abs(U));
           if (cross) atomicOr(&s_inf[node >> 5], 1u << (node & 31));
         }
         widx = (unsigned long long)j * P.Gs + (node >> 5);
@@ -817,7 +817,7 @@ k_bprologue_bounds(BatchState S, int32_t n, int32_t count, int32_t Bp, const dou
         // Bounds that already cross: the crossing test of round 1 covers
         // every variable, and tightening cannot undo a crossing, so the
         // node is flagged now and ends after its first round.
-        if (cmp_key(L) > cmp_key(U) && (isint || L > U + eps_feas * fmax(1.0, fabs(U))))
+        if (cmp_key(L) > cmp_key(U) && (isint || L > U + eps_feas * d_max1abs(U)))
           atomicOr(&S.inf_bits[node >> 5], 1u << (node & 31));
       }
       sL[yy][tx] = L;
@@ -955,7 +955,7 @@ k_bslot_fill(BatchState S, const int32_t *slots, int32_t count, const double *st
       if (d_isfinite(L)) L = d_ceil_int(L - eps_int);
       if (d_isfinite(U)) U = d_floor_int(U + eps_int);
     }
-    if (cmp_key(L) > cmp_key(U) && (isint || L > U + eps_feas * fmax(1.0, fabs(U))))
+    if (cmp_key(L) > cmp_key(U) && (isint || L > U + eps_feas * d_max1abs(U)))
       atomicOr(&S.inf_bits[node >> 5], 1u << (node & 31));
     const int64_t e = j * Bp + node;
     put_entry(S, e, L, U, isint, tau_dn, eps_dn);

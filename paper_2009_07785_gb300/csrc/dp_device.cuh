@@ -26,6 +26,15 @@ __device__ __forceinline__ float f_inf() { return __uint_as_float(0x7F800000u); 
 __device__ __forceinline__ void dsplit(double x, unsigned &lo, unsigned &hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
 }
+
+// Sign change of a binary64 value on the integer pipe (exact).
+__device__ __forceinline__ double d_neg(double x) {
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  double r;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi ^ 0x80000000u));
+  return r;
+}
 __device__ __forceinline__ bool d_isinf(double x) {
   unsigned lo, hi;
   dsplit(x, lo, hi);
@@ -111,7 +120,7 @@ __device__ __forceinline__ double d_floor_int(double x) {
   return __longlong_as_double((long long)t);
 }
 __device__ __forceinline__ double d_ceil_int(double x) {
-  return -d_floor_int(-x);
+  return d_neg(d_floor_int(d_neg(x)));
 }
 // x > y for non-NaN binary64 values, on the integer pipe: order-preserving
 // keys with -0 folded onto +0 (IEEE comparison treats them as equal).
@@ -127,8 +136,12 @@ __device__ __forceinline__ bool d_abs_lt(double x, double t) {
 }
 // max(1, |x|) for non-NaN x, by selection.
 __device__ __forceinline__ double d_max1abs(double x) {
-  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  return a >= 0x3FF0000000000000ull ? __longlong_as_double((long long)a) : 1.0;
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  hi &= 0x7FFFFFFFu;  // |x| >= 1 iff its high word is at least that of 1.0
+  double a;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(a) : "r"(lo), "r"(hi));
+  return hi >= 0x3FF00000u ? a : 1.0;
 }
 
 // A binary32 value >= x, from the bit pattern b of x (IEEE 754 field
@@ -262,15 +275,6 @@ __device__ __forceinline__ void set_flag(int32_t *f) {
   __threadfence();
 }
 
-// Sign change of a binary64 value on the integer pipe (exact).
-__device__ __forceinline__ double d_neg(double x) {
-  unsigned lo, hi;
-  dsplit(x, lo, hi);
-  double r;
-  asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi ^ 0x80000000u));
-  return r;
-}
-
 // ------------------------------------------------------- per-row decisions --
 
 // What the candidate step needs to know about one row (kept in shared
@@ -296,7 +300,7 @@ __device__ __forceinline__ bool row_sides_eval(RowView &rv, float Tr, float Tl,
     } else {
       double s = rv.rhs - rv.minfin;
       if (__double2hiint(s) < 0) {  // s < 0 (or -0, harmless)
-        double thr = rv.rhs + eps_feas * fmax(1.0, fabs(rv.rhs));
+        double thr = rv.rhs + eps_feas * d_max1abs(rv.rhs);
         if (rv.minfin > thr) infeas = true;
       }
       float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up_abs(rv.rhs), f32_up_abs(rv.minfin)));
@@ -310,7 +314,7 @@ __device__ __forceinline__ bool row_sides_eval(RowView &rv, float Tr, float Tl,
     } else {
       double s = rv.maxfin - rv.lhs;
       if (__double2hiint(s) < 0) {
-        double thr = rv.lhs - eps_feas * fmax(1.0, fabs(rv.lhs));
+        double thr = rv.lhs - eps_feas * d_max1abs(rv.lhs);
         if (rv.maxfin < thr) infeas = true;
       }
       float mg = __fmul_ru(0x1p-39f, __fadd_ru(f32_up_abs(rv.lhs), f32_up_abs(rv.maxfin)));

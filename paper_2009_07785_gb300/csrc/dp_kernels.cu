@@ -484,7 +484,7 @@ __device__ __forceinline__ void finish_var(const DevState &S, const uint8_t *var
   double L = val_of_key(kk.x), U = val_of_key(kk.y);
   uint32_t vt = vartype[j] ? 1u : 0u;
   if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
-    bool cross = vt ? (L > U) : (L > U + eps_feas * fmax(1.0, fabs(U)));
+    bool cross = vt ? (L > U) : (L > U + eps_feas * d_max1abs(U));
     if (cross) set_flag(inf_flag);
   }
   write_var(S.rec + j, L, U, vt, tau_dn, eps_dn);
