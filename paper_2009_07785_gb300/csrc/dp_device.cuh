@@ -35,6 +35,13 @@ __device__ __forceinline__ double d_neg(double x) {
   asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi ^ 0x80000000u));
   return r;
 }
+// The 64-bit pattern of a binary64 value, assembled from its halves so that
+// sign flips, masks and zero tests on it stay integer operations.
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  return ((unsigned long long)hi << 32) | lo;
+}
 __device__ __forceinline__ bool d_isinf(double x) {
   unsigned lo, hi;
   dsplit(x, lo, hi);
@@ -89,9 +96,13 @@ __device__ __forceinline__ bool d_pos(double a) {
 
 // Order-preserving map between binary64 values and signed 64-bit keys, so
 // that integer atomicMax/atomicMin implement max/min of doubles.
+// (Built from the two 32-bit halves: sign and zero tests on the 64-bit
+// pattern of a binary64 value can be turned into binary64 comparisons.)
 __device__ __forceinline__ long long key_of(double x) {
-  long long b = __double_as_longlong(x);
-  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  const unsigned m = (unsigned)((int)hi >> 31);  // all ones for a negative value
+  return (long long)(((unsigned long long)(hi ^ (m >> 1)) << 32) | (lo ^ m));
 }
 __device__ __forceinline__ double val_of_key(long long k) {
   return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFll));
@@ -104,7 +115,7 @@ __device__ __forceinline__ double val_of_key(long long k) {
 // fraction field correctly bumps the exponent).  Keeps binary64 pipe time for
 // the arithmetic that needs it.
 __device__ __forceinline__ double d_floor_int(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long b = dbits(x);
   const int e = (int)((b >> 52) & 0x7FFull) - 1023;
   const bool neg = (b >> 63) != 0ull;
   if (e >= 52) return x;  // integral, infinite or NaN
@@ -125,14 +136,15 @@ __device__ __forceinline__ double d_ceil_int(double x) {
 // x > y for non-NaN binary64 values, on the integer pipe: order-preserving
 // keys with -0 folded onto +0 (IEEE comparison treats them as equal).
 __device__ __forceinline__ long long cmp_key(double x) {
-  long long b = __double_as_longlong(x);
-  if (((unsigned long long)b << 1) == 0ull) b = 0;
-  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+  unsigned lo, hi;
+  dsplit(x, lo, hi);
+  if (((hi << 1) | lo) == 0u) hi = 0u;  // -0 -> +0
+  const unsigned m = (unsigned)((int)hi >> 31);
+  return (long long)(((unsigned long long)(hi ^ (m >> 1)) << 32) | (lo ^ m));
 }
 // |x| < t for a positive (possibly infinite) t; false for NaN x.
 __device__ __forceinline__ bool d_abs_lt(double x, double t) {
-  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) <
-         (unsigned long long)__double_as_longlong(t);
+  return (dbits(x) & 0x7FFFFFFFFFFFFFFFull) < dbits(t);
 }
 // max(1, |x|) for non-NaN x, by selection.
 __device__ __forceinline__ double d_max1abs(double x) {
@@ -166,9 +178,6 @@ __device__ __forceinline__ float f32_up_bits(unsigned long long b) {
   return -__uint_as_float(t);
 }
 constexpr unsigned long long kSign64 = 0x8000000000000000ull;
-__device__ __forceinline__ unsigned long long dbits(double x) {
-  return (unsigned long long)__double_as_longlong(x);
-}
 __device__ __forceinline__ float f32_up(double x) { return f32_up_bits(dbits(x)); }
 // a binary32 value <= x
 __device__ __forceinline__ float f32_dn(double x) { return -f32_up_bits(dbits(x) ^ kSign64); }
