@@ -105,3 +105,7 @@ def test_host_side_argument_checks(lib):
         assert L.dp_matrix_load_merge(None, 0, 0, 0, None, None, None, ipt, None, None,
                                       ctypes.byref(out)) == dp.DP_ERR_INVALID_ARG
         assert out.value is None
+    best = dp.dp_tune_entry()
+    for nodes in (0, 4):  # null context, and no nodes
+        assert L.dp_autotune_nodes(None, 0, 0, 0, None, None, None, nodes, None, None, None, None,
+                                   None, None, None, 0, None, best) == dp.DP_ERR_INVALID_ARG
