@@ -112,30 +112,38 @@ __device__ __forceinline__ bool warp_enqueue(const RowView &mine, const Top2 &t,
   for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(kFull, maxlen, o));
   const int64_t vo = elem0;
   const int32_t *cp = col + elem0;
-  for (int k = 0; k < maxlen; k += 4) {
-    double a[4];
-    int32_t j[4];
+  // software-pipelined: the next group's values and columns are fetched
+  // while this group's records are gathered
+  double an[4];
+  int32_t jn[4];
+  auto fetch = [&](int k0) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      a[u] = 1.0;
-      j[u] = 0;
-      if (k + u < len) {
-        a[u] = ld_coef(M, vo + (int64_t)(k + u) * kStride);
-        j[u] = cp[(int64_t)(k + u) * kStride];
+      an[u] = 1.0;
+      jn[u] = 0;
+      if (k0 + u < len) {
+        an[u] = ld_coef(M, vo + (int64_t)(k0 + u) * kStride);
+        jn[u] = cp[(int64_t)(k0 + u) * kStride];
       }
     }
+  };
+  if (maxlen > 0) fetch(0);
+  for (int k = 0; k < maxlen; k += 4) {
+    double a[4], L[4], U[4];
+    float WU[4], WL[4];
+    uint32_t fl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = an[u];
+      L[u] = U[u] = 0.0;
+      WU[u] = WL[u] = 0.0f;
+      if (k + u < len) ld_rec(S.rec + jn[u], L[u], U[u], WU[u], WL[u], fl[u]);
+    }
+    if (k + 4 < maxlen) fetch(k + 4);
     unsigned sd[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      sd[u] = 0u;
-      if (k + u < len) {
-        double L, U;
-        float WU, WL;
-        uint32_t fl;
-        ld_rec(S.rec + j[u], L, U, WU, WL, fl);
-        sd[u] = nnz_sides(a[u], L, U, WU, WL, mine);
-      }
-    }
+    for (int u = 0; u < 4; ++u)
+      sd[u] = k + u < len ? nnz_sides(a[u], L[u], U[u], WU[u], WL[u], mine) : 0u;
     // one reservation for the group's survivors of all lanes
     int c = 0;
 #pragma unroll
