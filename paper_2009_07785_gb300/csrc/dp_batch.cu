@@ -203,13 +203,31 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
   const double2 *bp = S.cur + node;
   const float2 *wp = S.wid + node;
   int k = 0;
+  // software-pipelined: the next group's values and columns are fetched
+  // while this group's bounds are gathered
+  double an[4];
+  int32_t jn[4];
+  if (len >= 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      an[u] = __ldg(vp + (int64_t)u * kSliceW);
+      jn[u] = __ldg(cp + (int64_t)u * kSliceW);
+    }
+  }
   for (; k + 4 <= len; k += 4) {
     double a[4];
     int32_t j[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      a[u] = __ldg(vp + (int64_t)(k + u) * kSliceW);
-      j[u] = __ldg(cp + (int64_t)(k + u) * kSliceW);
+      a[u] = an[u];
+      j[u] = jn[u];
+    }
+    if (k + 8 <= len) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        an[u] = __ldg(vp + (int64_t)(k + 4 + u) * kSliceW);
+        jn[u] = __ldg(cp + (int64_t)(k + 4 + u) * kSliceW);
+      }
     }
     double2 b[4];
     float2 w[4];
