@@ -180,10 +180,11 @@ def kernel_source_sha():
     return hashlib.sha256(data).hexdigest()[:16]
 
 
-def ncu_traffic():
-    """Per-launch DRAM bytes of k_round from the committed ncu summary, or
-    None if the kernel source changed since that capture."""
-    f = ROOT / "profiles" / "ncu_k_round_large.md"
+def ncu_traffic(chunk):
+    """Per-launch DRAM bytes of k_round from the committed ncu summary of the
+    same row split length, or None if there is none or the kernel source
+    changed since that capture."""
+    f = ROOT / "profiles" / f"ncu_k_round_large_chunk{chunk}.md"
     if not f.exists():
         return None
     h = kernel_source_sha()
@@ -746,7 +747,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     ach = b_round / (kms["round"] * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(ach / peak, 4), "traffic": ncu_traffic(),
+            "frac": round(ach / peak, 4), "traffic": ncu_traffic(chunk or 256),
             "kernel": "k_round", "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": b_round, "avg_launch_us": round(kms["round"] * 1e3, 2)}
 
