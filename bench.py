@@ -180,6 +180,20 @@ def kernel_source_sha():
     return hashlib.sha256(data).hexdigest()[:16]
 
 
+def read_summary(path):
+    """The `- key: `value`` lines of a profile summary as a dict (the value
+    between the backticks; a remark may follow it)."""
+    kv = {}
+    for line in Path(path).read_text().splitlines():
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            v = v.strip()
+            if v.startswith("`") and "`" in v[1:]:
+                v = v[1:v.index("`", 1)]
+            kv[k.strip()] = v
+    return kv
+
+
 def ncu_traffic(chunk):
     """Per-launch DRAM bytes of k_round from the committed ncu summary of the
     same row split length, or None if there is none or the kernel source
@@ -187,14 +201,8 @@ def ncu_traffic(chunk):
     f = ROOT / "profiles" / f"ncu_k_round_large_chunk{chunk}.md"
     if not f.exists():
         return None
-    h = kernel_source_sha()
-    text = f.read_text()
-    kv = {}
-    for line in text.splitlines():
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
-            kv[k.strip()] = v.strip().strip("`")
-    if kv.get("kernel_source_sha256_16") != h:
+    kv = read_summary(f)
+    if kv.get("kernel_source_sha256_16") != kernel_source_sha():
         return None
     try:
         return float(kv["dram_bytes_per_launch_full_size"])

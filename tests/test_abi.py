@@ -109,3 +109,16 @@ def test_host_side_argument_checks(lib):
     for nodes in (0, 4):  # null context, and no nodes
         assert L.dp_autotune_nodes(None, 0, 0, 0, None, None, None, nodes, None, None, None, None,
                                    None, None, None, 0, None, best) == dp.DP_ERR_INVALID_ARG
+
+
+def test_profile_summaries_parse():
+    """The bench reads k_round's DRAM traffic from the committed summaries:
+    each names the kernel sources it was taken from and a byte count."""
+    import bench
+
+    files = sorted((Path(__file__).resolve().parents[1] / "profiles").glob("ncu_k_round_large_chunk*.md"))
+    assert files
+    for f in files:
+        kv = bench.read_summary(f)
+        assert re.fullmatch(r"[0-9a-f]{16}", kv["kernel_source_sha256_16"])
+        assert float(kv["dram_bytes_per_launch_full_size"]) > 1e8
