@@ -11,8 +11,9 @@
 //                chunk (Def. 1, Eq. 2a/2b, Sec. 3.4 infinity counts); for
 //                whole rows also Step 2 and the binary32 screen, which
 //                queues the nonzeros whose candidates may be accepted
-//   k_combine    one warp per split row: sums the chunk partials in a fixed
-//                order, Step 2 and screen for the row
+//   k_combine    split rows of few pieces one per lane, rows of many pieces
+//                one per warp: sums the chunk partials in a fixed order,
+//                Step 2 and screen for the row
 //   k_cand_split one lane per chunk of an active split row: queueing
 //   k_cand_queue one thread per queued nonzero: the candidates (Eq. 3a/3b
 //                via Eq. 5a/5b) with filtered atomics (Sec. 3.5); marks the
@@ -311,91 +312,50 @@ k_round(DevMatrix M, DevState S) {
 // ------------------------------------------------------------ k_combine --
 
 constexpr int kCombineWarps = 8;
-constexpr int kCombineShort = 4;  // rows with at most this many pieces: one lane
+constexpr int kCombineShort = 4;  // rows with at most this many pieces: their own lane
 
-// One split row (warp-level).
-template <bool kMulti>
-__device__ __forceinline__ void combine_row(const DevMatrix &M, const DevState &S, int w) {
-  const Ctrl *ctrl = S.ctrl;
-  const int lane = threadIdx.x & 31;
-  const int32_t cb = M.split_cbeg[w], ce = M.split_cbeg[w + 1];
-  int32_t *inf_flag = &S.ctrl->infeasible;
-  if (kMulti) {
-    const int32_t inst = S.I.slot_inst[M.split_cidx[cb]];
-    if (S.I.done[inst]) {  // a stopped problem: no candidates
-      if (lane == 0) S.rowtot[w].active = 0;
-      return;
-    }
-    inf_flag = &S.I.infeasible[inst];
-  }
-  double mnf = 0.0, mxf = 0.0;
-  int32_t mni = 0, mxi = 0, ex = 0;
-  float Tr = -f_inf(), Tl = -f_inf();
-  auto add = [&](const Partial &p) {
-    mnf += p.minfin;
-    mxf += p.maxfin;
-    mni += p.mininf;
-    mxi += p.maxinf;
-    Tr = fmaxf(Tr, p.t.r1);
-    Tl = fmaxf(Tl, p.t.l1);
-    ex |= p.exact;
-  };
-  if (ce - cb <= kCombineShort) {
-    // most split rows have two or three pieces: one lane sums them in piece
-    // order (no cross-lane reduction, whose shuffles dominate otherwise)
-    if (lane != 0) return;
-    Partial p[kCombineShort];
-#pragma unroll
-    for (int u = 0; u < kCombineShort; ++u)
-      if (cb + u < ce) p[u] = S.part[M.split_cidx[cb + u]];
-#pragma unroll
-    for (int u = 0; u < kCombineShort; ++u)
-      if (cb + u < ce) add(p[u]);
-  } else {
-    // each lane sums its pieces in order; the loads of four pieces are
-    // issued before they are consumed
-    int32_t q = cb + lane;
-    for (; q + 3 * kSliceW < ce; q += 4 * kSliceW) {
-      int32_t ci[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) ci[u] = M.split_cidx[q + u * kSliceW];
-      Partial p[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) p[u] = S.part[ci[u]];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) add(p[u]);
-    }
-    for (; q < ce; q += kSliceW) add(S.part[M.split_cidx[q]]);
-    // butterfly reduction: a fixed pattern, so the sum is reproducible and
-    // identical in every lane (binary64 addition is commutative)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      mnf += __shfl_xor_sync(kFull, mnf, off);
-      mxf += __shfl_xor_sync(kFull, mxf, off);
-      mni += __shfl_xor_sync(kFull, mni, off);
-      mxi += __shfl_xor_sync(kFull, mxi, off);
-      Tr = fmaxf(Tr, __shfl_xor_sync(kFull, Tr, off));
-      Tl = fmaxf(Tl, __shfl_xor_sync(kFull, Tl, off));
-      ex |= __shfl_xor_sync(kFull, ex, off);
-    }
-  }
-  if (lane != 0) return;
+// Running sums of a split row's pieces.
+struct RowAcc {
+  double mnf, mxf;
+  int32_t mni, mxi, ex;
+  float Tr, Tl;
+};
+
+__device__ __forceinline__ void acc_init(RowAcc &a) {
+  a.mnf = a.mxf = 0.0;
+  a.mni = a.mxi = a.ex = 0;
+  a.Tr = a.Tl = -f_inf();
+}
+
+__device__ __forceinline__ void acc_add(RowAcc &a, const Partial &p) {
+  a.mnf += p.minfin;
+  a.mxf += p.maxfin;
+  a.mni += p.mininf;
+  a.mxi += p.maxinf;
+  a.Tr = fmaxf(a.Tr, p.t.r1);
+  a.Tl = fmaxf(a.Tl, p.t.l1);
+  a.ex |= p.exact;
+}
+
+// Step 2 and the screen thresholds of split row w from its sums (thread-level).
+__device__ __forceinline__ void combine_commit(const DevMatrix &M, const DevState &S, int64_t w,
+                                               RowAcc &a, int32_t *inf_flag) {
   const int32_t row = M.split_row[w];
   RowView rv;
-  rv.minfin = mnf;
-  rv.maxfin = mxf;
-  rv.mininf = mni;
-  rv.maxinf = mxi;
+  rv.minfin = a.mnf;
+  rv.maxfin = a.mxf;
+  rv.mininf = a.mni;
+  rv.maxinf = a.mxi;
   rv.lhs = S.lhs[row];
   rv.rhs = S.rhs[row];
-  rv.exact = ex;
-  if (ex) Tr = Tl = f_inf();
-  row_sides(rv, Tr, Tl, ctrl->eps_feas, inf_flag);
+  rv.exact = a.ex;
+  if (a.ex) a.Tr = a.Tl = f_inf();
+  row_sides(rv, a.Tr, a.Tl, S.ctrl->eps_feas, inf_flag);
   RowTot rt;
-  rt.minfin = mnf;
-  rt.maxfin = mxf;
-  rt.mininf = mni;
-  rt.maxinf = mxi;
+  rt.minfin = a.mnf;
+  rt.maxfin = a.mxf;
+  rt.mininf = a.mni;
+  rt.maxinf = a.mxi;
   rt.thr_r = rv.thr_r;
   rt.thr_l = rv.thr_l;
   rt.active = rv.act;
@@ -403,13 +363,86 @@ __device__ __forceinline__ void combine_row(const DevMatrix &M, const DevState &
   S.rowtot[w] = rt;
 }
 
+// Warp w of the split-row pass (warp-level, all 32 lanes): rows [32w,
+// 32w + 32) of at most kCombineShort pieces are summed each by its own lane
+// in piece order; row w, if it has more pieces, by the whole warp, lanes
+// strided over its pieces and then a fixed butterfly (reproducible, and the
+// same in every lane).  Which of the two sums a row depends only on its
+// piece count, and every row is summed once.
+template <bool kMulti>
+__device__ __forceinline__ void combine_rows(const DevMatrix &M, const DevState &S, int64_t w) {
+  const int lane = threadIdx.x & 31;
+  auto flag_of = [&](int32_t first_piece) -> int32_t * {
+    return kMulti ? &S.I.infeasible[S.I.slot_inst[M.split_cidx[first_piece]]]
+                  : &S.ctrl->infeasible;
+  };
+  auto stopped = [&](int32_t first_piece) {  // a stopped problem: no candidates
+    return kMulti && S.I.done[S.I.slot_inst[M.split_cidx[first_piece]]];
+  };
+  // short rows, one per lane
+  const int64_t r = w * 32 + lane;
+  if (r < M.nsplit_rows) {
+    const int32_t cb = M.split_cbeg[r], ce = M.split_cbeg[r + 1];
+    if (ce - cb <= kCombineShort) {
+      if (stopped(cb)) {
+        S.rowtot[r].active = 0;
+      } else {
+        RowAcc a;
+        acc_init(a);
+        Partial p[kCombineShort];
+#pragma unroll
+        for (int u = 0; u < kCombineShort; ++u)
+          if (cb + u < ce) p[u] = S.part[M.split_cidx[cb + u]];
+#pragma unroll
+        for (int u = 0; u < kCombineShort; ++u)
+          if (cb + u < ce) acc_add(a, p[u]);
+        combine_commit(M, S, r, a, flag_of(cb));
+      }
+    }
+  }
+  // row w if it has many pieces (warp-uniform)
+  const int32_t b = M.split_cbeg[w], e = M.split_cbeg[w + 1];
+  if (e - b <= kCombineShort) return;
+  if (stopped(b)) {
+    if (lane == 0) S.rowtot[w].active = 0;
+    return;
+  }
+  RowAcc a;
+  acc_init(a);
+  // each lane sums its pieces in order; the loads of four pieces are issued
+  // before they are consumed
+  int32_t q = b + lane;
+  for (; q + 3 * kSliceW < e; q += 4 * kSliceW) {
+    int32_t ci[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ci[u] = M.split_cidx[q + u * kSliceW];
+    Partial p[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[u] = S.part[ci[u]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc_add(a, p[u]);
+  }
+  for (; q < e; q += kSliceW) acc_add(a, S.part[M.split_cidx[q]]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a.mnf += __shfl_xor_sync(kFull, a.mnf, off);
+    a.mxf += __shfl_xor_sync(kFull, a.mxf, off);
+    a.mni += __shfl_xor_sync(kFull, a.mni, off);
+    a.mxi += __shfl_xor_sync(kFull, a.mxi, off);
+    a.Tr = fmaxf(a.Tr, __shfl_xor_sync(kFull, a.Tr, off));
+    a.Tl = fmaxf(a.Tl, __shfl_xor_sync(kFull, a.Tl, off));
+    a.ex |= __shfl_xor_sync(kFull, a.ex, off);
+  }
+  if (lane == 0) combine_commit(M, S, w, a, flag_of(b));
+}
+
 template <bool kMulti>
 __global__ void __launch_bounds__(kCombineWarps * 32)
 k_combine(DevMatrix M, DevState S) {
   if (S.ctrl->err) return;
-  const int w = blockIdx.x * kCombineWarps + (threadIdx.x >> 5);
+  const int64_t w = blockIdx.x * (int64_t)kCombineWarps + (threadIdx.x >> 5);
   if (w >= M.nsplit_rows) return;  // warp-uniform
-  combine_row<kMulti>(M, S, w);
+  combine_rows<kMulti>(M, S, w);
 }
 
 // --------------------------------------------------------- k_cand_split --
@@ -659,7 +692,7 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
       for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, false>(M, S, sl);
     if (!grid_sync(S)) return;
     if (M.nsplit_rows > 0) {
-      for (int w = gw; w < M.nsplit_rows; w += nw) combine_row<false>(M, S, w);
+      for (int w = gw; w < M.nsplit_rows; w += nw) combine_rows<false>(M, S, w);
       if (!grid_sync(S)) return;
       for (int sl = gw; sl < M.nslices_split; sl += nw) cand_split_slice(M, S, sl);
       if (!grid_sync(S)) return;
@@ -815,7 +848,7 @@ cudaError_t launch_ell_front(const DevMatrix &M, const DevState &S, cudaStream_t
   if (ev) cudaEventRecord(ev[1], st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (M.nsplit_rows > 0) {
-    int nbc = (M.nsplit_rows + kCombineWarps - 1) / kCombineWarps;
+    int nbc = (M.nsplit_rows + kCombineWarps - 1) / kCombineWarps;  // a warp per row
     if (ev) cudaEventRecord(ev[2], st);
     k_combine<kMulti><<<nbc, kCombineWarps * 32, 0, st>>>(M, S);
     if (ev) cudaEventRecord(ev[3], st);
