@@ -172,12 +172,24 @@ def peaks():
     return PEAK_FALLBACK_GBS, "fallback"
 
 
+def source_sha(names):
+    """Hash of the code of csrc files, comments and whitespace removed (a
+    comment edit does not change what a profile capture measured)."""
+    import re
+
+    csrc = ROOT / "paper_2009_07785_gb300" / "csrc"
+    code = []
+    for f in names:
+        text = (csrc / f).read_text()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        code.append(" ".join(text.split()))
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
+
+
 def kernel_source_sha():
     """Hash of the sources that define k_round (kernel file + device helpers)."""
-    csrc = ROOT / "paper_2009_07785_gb300" / "csrc"
-    data = b"".join((csrc / f).read_bytes()
-                    for f in ("dp_kernels.cu", "dp_device.cuh", "dp_round.cuh"))
-    return hashlib.sha256(data).hexdigest()[:16]
+    return source_sha(("dp_kernels.cu", "dp_device.cuh", "dp_round.cuh"))
 
 
 def read_summary(path):

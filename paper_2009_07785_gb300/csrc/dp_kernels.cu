@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
 // ------------------------------------------------------------- k_round --
 
 // Warps per block of k_round / k_cand_split: a launch shape the autotuner
-// chooses (4 or 8); the register budget per thread stays the same (24
+// chooses (4 or 8); the register budget per thread stays the same (32
 // resident warps per SM).
-constexpr int kRoundWarpsPerSM = 24;
-constexpr int kGroup = 4;         // slots per group in the activity loop
+constexpr int kRoundWarpsPerSM = 32;
+constexpr int kGroup = 2;         // slots per group in the activity loop
 
 // One slice of the round (warp-level: the 32 lanes are its 32 chunks).
 // kVal8: the coefficients come from the int8 copy (converted when used, so
