@@ -149,14 +149,18 @@ __global__ void __launch_bounds__(256) k_cand_queue(DevMatrix M, DevState S) {
 
 // Warps per block of k_round / k_cand_split: a launch shape the autotuner
 // chooses (4 or 8); the register budget per thread stays the same (32
-// resident warps per SM).
+// resident warps per SM for a single problem, 24 for problem sets).
 constexpr int kRoundWarpsPerSM = 32;
 constexpr int kGroup = 2;         // slots per group in the activity loop
+// the problem-set variant (more live state per lane) and the persistent
+// kernel measured faster with fewer resident warps and longer groups
+constexpr int kRoundWarpsPerSMMulti = 24;
+constexpr int kGroupWide = 4;
 
 // One slice of the round (warp-level: the 32 lanes are its 32 chunks).
 // kVal8: the coefficients come from the int8 copy (converted when used, so
 // that the prefetched loads stay in flight).
-template <bool kMulti, bool kVal8>
+template <bool kMulti, bool kVal8, int kG = kGroup>
 __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &S, int slice) {
   const Ctrl *ctrl = S.ctrl;
   const int lane = threadIdx.x & 31;
@@ -191,7 +195,7 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
   double minfin = 0.0, maxfin = 0.0;
   int32_t mininf = 0, maxinf = 0;
   Top2 t = top2_init();
-  // groups of kGroup slots: all loads and gathers of a group are issued
+  // groups of kG slots: all loads and gathers of a group are issued
   // before any is consumed, and the next group's values and columns are
   // fetched while this group's gathers are in flight; the last group's
   // missing slots are skipped (uniformly within a length-sorted slice)
@@ -204,10 +208,10 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
     if constexpr (kVal8) return small_int_to_double(r);
     else return r;
   };
-  Raw an[kGroup];
-  int32_t jn[kGroup];
+  Raw an[kG];
+  int32_t jn[kG];
 #pragma unroll
-  for (int u = 0; u < kGroup; ++u) {
+  for (int u = 0; u < kG; ++u) {
     an[u] = (Raw)1;
     jn[u] = 0;
     if (u < len) {
@@ -215,31 +219,31 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
       jn[u] = __ldcs(cp + (int64_t)u * kSliceW);
     }
   }
-  for (int k = 0; k < len; k += kGroup) {
-    Raw a[kGroup];
-    double L[kGroup], U[kGroup];
-    float WU[kGroup], WL[kGroup];
-    uint32_t fl[kGroup];
+  for (int k = 0; k < len; k += kG) {
+    Raw a[kG];
+    double L[kG], U[kG];
+    float WU[kG], WL[kG];
+    uint32_t fl[kG];
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u) {
+    for (int u = 0; u < kG; ++u) {
       a[u] = an[u];
       L[u] = U[u] = 0.0;
       WU[u] = WL[u] = 0.0f;
       if (k + u < len) ld_rec(S.rec + jn[u], L[u], U[u], WU[u], WL[u], fl[u]);
     }
-    if (k + kGroup < len) {
+    if (k + kG < len) {
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) {
+      for (int u = 0; u < kG; ++u) {
         an[u] = (Raw)1;
         jn[u] = 0;
-        if (k + kGroup + u < len) {
-          an[u] = raw(vo + (int64_t)(k + kGroup + u) * kSliceW);
-          jn[u] = __ldcs(cp + (int64_t)(k + kGroup + u) * kSliceW);
+        if (k + kG + u < len) {
+          an[u] = raw(vo + (int64_t)(k + kG + u) * kSliceW);
+          jn[u] = __ldcs(cp + (int64_t)(k + kG + u) * kSliceW);
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < kGroup; ++u) {
+    for (int u = 0; u < kG; ++u) {
       if (k + u < len) {
         const double av = coef(a[u]);
         bool pos = d_pos(av);
@@ -301,12 +305,13 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
 }
 
 template <bool kMulti, int kRoundWarps, bool kVal8>
-__global__ void __launch_bounds__(kRoundWarps * 32, kRoundWarpsPerSM / kRoundWarps)
+__global__ void __launch_bounds__(kRoundWarps * 32,
+                                  (kMulti ? kRoundWarpsPerSMMulti : kRoundWarpsPerSM) / kRoundWarps)
 k_round(DevMatrix M, DevState S) {
   if (S.ctrl->err) return;
   const int slice = blockIdx.x * kRoundWarps + (threadIdx.x >> 5);
   if (slice >= M.nslices) return;  // warp-uniform
-  round_slice<kMulti, kVal8>(M, S, slice);
+  round_slice<kMulti, kVal8, kMulti ? kGroupWide : kGroup>(M, S, slice);
 }
 
 // ------------------------------------------------------------ k_combine --
@@ -687,9 +692,9 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
   for (;;) {
     if (M.val8)
-      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, true>(M, S, sl);
+      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, true, kGroupWide>(M, S, sl);
     else
-      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, false>(M, S, sl);
+      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, false, kGroupWide>(M, S, sl);
     if (!grid_sync(S)) return;
     if (M.nsplit_rows > 0) {
       for (int w = gw; w < M.nsplit_rows; w += nw) combine_rows<false>(M, S, w);
