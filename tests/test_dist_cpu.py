@@ -1,14 +1,12 @@
 """The multi-process (torchrun) path of bench.py on CPU with gloo, world size
 2: replicas time their own workload and the job takes the slowest rank's
 time; the reference arm runs on rank 0 only."""
-import json
 import os
 import socket
 import subprocess
 import sys
 from pathlib import Path
 
-import pytest
 
 ROOT = Path(__file__).resolve().parent.parent
 
