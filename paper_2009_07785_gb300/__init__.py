@@ -536,10 +536,27 @@ def dp_propagate_noalloc(device: int, stream, m: int, n: int, row_ptr, col_idx, 
     device memory (all array arguments are CUDA tensors; lb_out/ub_out are
     caller-allocated).  For callers that must not allocate device memory;
     its scratch is a fixed static device array (n <= NOALLOC_MAX_VARS)."""
+    import torch
+
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
+    m, n = int(m), int(n)
+    want = torch.device("cuda", int(device))
+    nnz = int(col_idx.numel()) if isinstance(col_idx, torch.Tensor) else -1
+    spec = (("row_ptr", row_ptr, torch.int64, m + 1), ("col_idx", col_idx, torch.int32, nnz),
+            ("val", val, torch.float64, nnz), ("lb", lb, torch.float64, n),
+            ("ub", ub, torch.float64, n), ("vartype", vartype, torch.uint8, n),
+            ("lhs", lhs, torch.float64, m), ("rhs", rhs, torch.float64, m),
+            ("lb_out", lb_out, torch.float64, n), ("ub_out", ub_out, torch.float64, n))
+    for name, t, dt, numel in spec:
+        # the C entry point reads raw device pointers: the element type, length
+        # and device must be right here, nothing converts them
+        if not (isinstance(t, torch.Tensor) and t.device == want and t.dtype == dt
+                and t.numel() == numel and t.is_contiguous()):
+            raise DomPropError(DP_ERR_INVALID_ARG,
+                               f"dp_propagate_noalloc: {name} must be a contiguous {dt} tensor "
+                               f"of {numel} elements on {want}")
     inf, rounds = C.c_int32(), C.c_int32()
-    nnz = int(col_idx.numel()) if hasattr(col_idx, "numel") else len(col_idx)
     rc = _check(lib().dp_propagate_noalloc(
         int(device), C.c_void_p(stream) if stream else None, int(m), int(n), nnz, _ptr(row_ptr),
         _ptr(col_idx), _ptr(val), _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs), _ptr(rhs),

@@ -16,6 +16,7 @@
 // what it uses.  Calls whose GPU work overlaps (two streams, two host
 // threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 
@@ -35,7 +36,11 @@ struct NoallocCtrl {
 };
 
 constexpr int kMaxDevices = 64;
-long long *g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
+// Device address of the array, per device.  Host threads that call the entry
+// point on different devices may fill their entries concurrently; the lookup
+// is idempotent, so an atomic store per entry is all the synchronisation it
+// needs.
+std::atomic<long long *> g_scratch_addr[kMaxDevices] = {};
 
 __device__ __forceinline__ bool is_inf_d(double x) {
   return ((unsigned long long)__double_as_longlong(x) << 1) == 0xFFE0000000000000ull;
@@ -189,30 +194,54 @@ __global__ void k_na_finish(int32_t n, const uint8_t *vt, const long long *keys,
   hi[j] = U;
 }
 
-bool on_device(const void *p) {
+// Device memory that `device` can read without peer access: memory allocated
+// on that device, or managed memory.  A pointer to another GPU's memory is
+// refused (reading it would need peer access the library never enables).
+bool on_device(const void *p, int device) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 // Device address of the scratch array on `device` (which must be current);
 // looked up once per device.
 long long *scratch_on(int device) {
   if (device < 0 || device >= kMaxDevices) return nullptr;
-  if (!g_scratch_addr[device]) {
+  long long *addr = g_scratch_addr[device].load(std::memory_order_acquire);
+  if (!addr) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
-    g_scratch_addr[device] = static_cast<long long *>(p);
+    addr = static_cast<long long *>(p);
+    g_scratch_addr[device].store(addr, std::memory_order_release);
   }
-  return g_scratch_addr[device];
+  return addr;
 }
+
+// Makes `device` current for its lifetime and gives the caller's current
+// device back on every return path.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    ok = cudaSetDevice(device) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 int grid(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
@@ -247,16 +276,15 @@ extern "C" int dp_propagate_noalloc(int device, void *cuda_stream, int32_t m, in
   if (p.max_rounds < 0 || !(p.eps_int >= 0) || !(p.tau_rel >= 0) || !(p.eps_feas >= 0) ||
       !(p.inf_threshold > 0))
     return DP_ERR_INVALID_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) {
-    cudaGetLastError();
+  DeviceGuard guard(device);
+  if (!guard.ok) return DP_ERR_INVALID_ARG;
+  auto dev_ok = [device](const void *q) { return on_device(q, device); };
+  if (!dev_ok(row_ptr) || (nnz > 0 && (!dev_ok(col_idx) || !dev_ok(val))))
     return DP_ERR_INVALID_ARG;
-  }
-  if (!on_device(row_ptr) || (nnz > 0 && (!on_device(col_idx) || !on_device(val))))
+  if (n > 0 && (!dev_ok(lb) || !dev_ok(ub) || !dev_ok(vartype) || !dev_ok(lb_out) ||
+                !dev_ok(ub_out)))
     return DP_ERR_INVALID_ARG;
-  if (n > 0 && (!on_device(lb) || !on_device(ub) || !on_device(vartype) || !on_device(lb_out) ||
-                !on_device(ub_out)))
-    return DP_ERR_INVALID_ARG;
-  if (m > 0 && (!on_device(lhs) || !on_device(rhs))) return DP_ERR_INVALID_ARG;
+  if (m > 0 && (!dev_ok(lhs) || !dev_ok(rhs))) return DP_ERR_INVALID_ARG;
   long long *scratch = scratch_on(device);
   if (!scratch) return DP_ERR_CUDA;
   long long *keys = scratch;
