@@ -22,6 +22,22 @@ MUTANTS = {
     "round_count_off_by_one": ("*rounds = r;", "*rounds = r - 1;"),
     "lhs_side_dropped": ("if (isfinite(lhs[i]) && isfinite(resmax)) { lc = (lhs[i] - resmax) / a;",
                          "if (0) { lc = (lhs[i] - resmax) / a;"),
+    # the infinity-threshold readings: >= turned into >, a dropped discard,
+    # a sign slip on the -inf_threshold side
+    "input_ub_threshold_strict": ("if (ub[j] >= inf_threshold) ub[j] = INFINITY;",
+                                  "if (ub[j] > inf_threshold) ub[j] = INFINITY;"),
+    "input_lb_threshold_strict": ("if (lb[j] <= -inf_threshold) lb[j] = -INFINITY;",
+                                  "if (lb[j] < -inf_threshold) lb[j] = -INFINITY;"),
+    "input_rhs_threshold_strict": ("if (rhs[i] >= inf_threshold) rhs[i] = INFINITY;",
+                                   "if (rhs[i] > inf_threshold) rhs[i] = INFINITY;"),
+    "input_lhs_threshold_sign": ("if (lhs[i] <= -inf_threshold) lhs[i] = -INFINITY;",
+                                 "if (-lhs[i] <= -inf_threshold) lhs[i] = -INFINITY;"),
+    "upper_candidate_threshold_strict": ("if (isfinite(uc) && fabs(uc) >= inf_threshold) {",
+                                         "if (isfinite(uc) && fabs(uc) > inf_threshold) {"),
+    "lower_candidate_threshold_strict": ("if (isfinite(lc) && fabs(lc) >= inf_threshold) {",
+                                         "if (isfinite(lc) && fabs(lc) > inf_threshold) {"),
+    "upper_candidate_discard_dropped": ("        uc = INFINITY;\n      } else if", "        ;\n      } else if"),
+    "lower_candidate_discard_dropped": ("        lc = -INFINITY;\n      } else if", "        ;\n      } else if"),
     "live_reads_in_candidates": ("      double bmin = (a > 0.0) ? L[j] : U[j];\n      double bmax = (a > 0.0) ? U[j] : L[j];\n\n      /* residual",
                                  "      double bmin = (a > 0.0) ? Lnew[j] : Unew[j];\n      double bmax = (a > 0.0) ? Unew[j] : Lnew[j];\n\n      /* residual"),
 }

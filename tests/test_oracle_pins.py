@@ -290,3 +290,58 @@ def test_rejects_nan(orc):
     inst.lb[3] = np.nan
     with pytest.raises(ValueError):
         orc.propagate_instance(inst)
+
+
+def _reorder_rows(row_ptr, col, val, rng, mode):
+    """The same matrix with every row's nonzeros in another order (reversed
+    or shuffled): the row sums of Eq. 2 are then taken in another order."""
+    col2, val2 = col.copy(), val.copy()
+    for i in range(len(row_ptr) - 1):
+        b, e = int(row_ptr[i]), int(row_ptr[i + 1])
+        perm = np.arange(b, e)[::-1] if mode == "reversed" else rng.permutation(np.arange(b, e))
+        col2[b:e], val2[b:e] = col[perm], val[perm]
+    return col2, val2
+
+
+@pytest.mark.parametrize("mode", ["reversed", "shuffled"])
+def test_reordering_error_bound_covers_other_summation_orders(orc, mode):
+    """The round analysis bounds how far a bound may move when the row sums
+    are taken in another order.  Summing every row in another order (the
+    same arithmetic, only reassociated) must move each new bound by at most
+    that bound, must leave integer bounds and acceptance decisions alone
+    unless flagged as a tie (and few flagged decisions may actually flip),
+    and the bound must not be vacuous: over the instance the largest
+    observed move is within 10^3 of it."""
+    rng = np.random.default_rng(2024 if mode == "reversed" else 2025)
+    inst = synth.medium(seed=synth.seed_for(1, 17), scale=0.02)  # fractional coefficients
+    L, U, lhs, rhs = orc.normalise(inst.m, inst.n, inst.lb, inst.ub, inst.vartype, inst.lhs,
+                                   inst.rhs)
+    ratio_max, checked, ties_used = 0.0, 0, 0
+    for _ in range(4):  # the first rounds, from the oracle's own states
+        a = orc.round_(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, L, U, inst.vartype,
+                       lhs, rhs, analysis=True)
+        c2, v2 = _reorder_rows(inst.row_ptr, inst.col, inst.val, rng, mode)
+        b = orc.round_(inst.m, inst.n, inst.row_ptr, c2, v2, L, U, inst.vartype, lhs, rhs)
+        for new_a, new_b, err, tie in ((a.lb, b.lb, a.lb_err, a.lb_tie), (a.ub, b.ub, a.ub_err,
+                                                                            a.ub_tie)):
+            tie = tie.astype(bool)
+            isint = inst.vartype.astype(bool)
+            with np.errstate(invalid="ignore"):
+                d = np.abs(new_a - new_b)
+            both_inf = np.isinf(new_a) & (new_a == new_b)
+            within = both_inf | np.where(isint, d == 0.0, d <= err)
+            # a move beyond the bound is a decision that went the other way,
+            # which only a tie may do
+            assert np.all(within | tie), "a bound moved beyond its error bound without a tie"
+            ties_used += int((~within).sum())
+            sel = ~isint & ~both_inf & (err > 0)
+            checked += int(sel.sum())
+            if sel.any():
+                ratio_max = max(ratio_max, float((d[sel] / err[sel]).max()))
+        assert b.infeasible == a.infeasible or a.inf_tie
+        if not a.changed:
+            break
+        L, U = a.lb, a.ub
+    assert checked > 100
+    assert ties_used <= 5  # decisions that actually went the other way
+    assert ratio_max >= 1e-3, f"the error bound is over 10^3 times the largest move ({ratio_max})"
