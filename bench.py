@@ -13,8 +13,11 @@ e2e     : the same metric through the same public call with pinned HOST
 roofline: the activity/candidate kernel (k_round), algorithmic bytes
           12*nnz + 20*m per launch over its CUDA-event launch time, taken
           with the host-driven loop variant right after the timed region.
-cpu_baseline / --impl reference: the CPU oracle (one thread) on a bounded
-          number of rounds of the same workload.
+cpu_baseline: the CPU oracle (one thread) propagating the same workload in
+          full; its bounds are also compared element by element with the
+          GPU's (`parity`: integer bounds and the infeasibility flag exact,
+          continuous within 1e-9 relative).
+--impl reference: the oracle, one round over a 1/16 row block per step.
 value_compression: the same propagation reading the lossless int8 copy of
           the (small-integer) coefficients: 5 streamed bytes per nonzero
           instead of 12 (reported apart from the roofline fraction).
@@ -115,7 +118,6 @@ def parse():
                     help="skip the autotuner (chunk 256, 8 warps per block)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (profiling captures only; the bench line uses 1.0)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compression", action="store_true",
@@ -295,22 +297,46 @@ def job_value(units_per_rank: float, ranks: int, seconds_max: float) -> float:
     return units_per_rank * ranks / seconds_max
 
 
-def cpu_oracle_rounds(inst, seconds):
-    """Times oracle rounds from the initial bounds until `seconds` elapse or
-    the fixed point; returns (rounds, elapsed)."""
+def oracle_propagation(inst):
+    """The oracle's whole propagation of the workload from its initial bounds
+    to its fixed point, timed from the first round to the result (its
+    normalisation included); returns (result, seconds)."""
     import oracle
 
-    L, U, lhs, rhs = oracle.normalise(inst.m, inst.n, inst.lb, inst.ub, inst.vartype, inst.lhs,
-                                      inst.rhs)
-    r, t0 = 0, time.perf_counter()
-    while True:
-        rr = oracle.round_(inst.m, inst.n, inst.row_ptr, inst.col, inst.val, L, U, inst.vartype,
-                           lhs, rhs)
-        r += 1
-        L, U = rr.lb, rr.ub
-        el = time.perf_counter() - t0
-        if el >= seconds or not rr.changed or rr.infeasible:
-            return r, el
+    t0 = time.perf_counter()
+    o = oracle.propagate_instance(inst)
+    return o, time.perf_counter() - t0
+
+
+# parity tolerance (the same as the tests'): integer bounds and the
+# infeasibility flag exactly, continuous bounds within max(1e-12, 1e-9 |oracle|)
+PARITY_REL, PARITY_ABS = 1e-9, 1e-12
+
+
+def parity_vs_oracle(inst, g_lb, g_ub, g_rounds, g_infeasible, o):
+    """Element-by-element comparison of the GPU's propagation with the
+    oracle's, both run independently from the same initial bounds."""
+    isint = inst.vartype.astype(bool)
+    bad, rel_max = 0, 0.0
+    for g, r in ((g_lb, o.lb), (g_ub, o.ub)):
+        same = (g == r)  # equal, including equal infinities
+        with np.errstate(invalid="ignore"):
+            d = np.abs(g - r)
+        tol = np.maximum(PARITY_ABS, PARITY_REL * np.abs(r))
+        ok = np.where(isint, same, same | (d <= tol))
+        bad += int((~ok).sum())
+        fin = np.isfinite(g) & np.isfinite(r) & ~isint
+        if fin.any():
+            rel_max = max(rel_max, float((d[fin] / np.maximum(1.0, np.abs(r[fin]))).max()))
+    return {"mode": "independent full propagations from the same initial bounds",
+            "rounds_gpu": int(g_rounds), "rounds_oracle": int(o.rounds),
+            "infeasible_gpu": int(g_infeasible), "infeasible_oracle": int(o.infeasible),
+            "bounds_compared": int(2 * inst.n), "n_bad": bad, "n_ties_used": 0,
+            "max_rel_diff_continuous": rel_max,
+            "tolerance": "integer bounds and the infeasibility flag exact; continuous "
+                         "within max(1e-12, 1e-9 |oracle|)",
+            "ok": bad == 0 and int(g_rounds) == int(o.rounds)
+                  and int(g_infeasible) == int(o.infeasible)}
 
 
 def run_reference(args):
@@ -685,6 +711,7 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3)):
         r = step()
     rounds = r.rounds
+    head = (d_lb.clone(), d_ub.clone(), r.rounds, r.infeasible)  # kept for the parity check
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -791,12 +818,14 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": el * 1e3 / ke}
 
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        r_cpu, el = cpu_oracle_rounds(inst, args.cpu_seconds)
-        cpu = {"value": inst.nnz * r_cpu / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {r_cpu} of {rounds} rounds of the same workload from its initial "
-                         f"bounds, single-threaded C oracle ({el:.1f} s)"}
+        o, el = oracle_propagation(inst)
+        cpu = {"value": inst.nnz * o.rounds / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the whole propagation of the same workload ({o.rounds} rounds from "
+                         f"its initial bounds), single-threaded C oracle ({el:.1f} s)"}
+        parity = parity_vs_oracle(inst, head[0].cpu().numpy(), head[1].cpu().numpy(), head[2],
+                                  head[3], o)
 
     nodes = None
     if ws == 1 and not args.no_nodes:
@@ -822,7 +851,8 @@ def run_ours(args):
                           "hostloop_ms_per_step": round(hostloop_ms, 3),
                           "l2": "no flush: the matrix streamed each round (0.36 GB) exceeds the 129 MB L2",
                           "parallelism": f"replicas x{ws}"},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "roofline": roof, "cpu_baseline": cpu, "parity": parity, "e2e": e2e,
+               "gpu_launches": launches,
                "clocks": clk, "value_compression": compression,
                "persistent_loop": persistent, "merge_path": merge, "batched_nodes": nodes,
                "batched_matrices": sets,

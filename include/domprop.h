@@ -342,6 +342,32 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
                           float *kernel_ms, int32_t *kernel_launches);
 
 /*
+ * Failure detection and test hooks.  The paper has no counterpart; these
+ * exist so that the library's bounded waits and its clean-up after a
+ * failed allocation can be tested without faulting a GPU.
+ *
+ * dp_ctx_set_wait_limit: a block of the persistent round loop
+ * (dp_propagate_persistent) waits at a grid barrier for at most `sleeps`
+ * sleeps of about 64 ns before it records DP_ERR_TIMEOUT and every block
+ * leaves the kernel; the call then returns DP_ERR_TIMEOUT and the context
+ * stays usable.  0 restores the default (2^25 sleeps, about 2 s).  Under a
+ * cooperative launch every block is resident, so the default is never
+ * reached unless something is wrong; a test sets a few sleeps to make the
+ * wait run out.  Returns DP_OK or DP_ERR_INVALID_ARG (ctx NULL, sleeps < 0).
+ *
+ * dp_debug_fail_alloc: the k-th device allocation the library makes from
+ * now on (k >= 1, process-wide, counted over every context) fails as if the
+ * device were out of memory, so that the caller sees DP_ERR_OOM; k = 0
+ * disarms.  Returns DP_OK or DP_ERR_INVALID_ARG (k < 0).
+ *
+ * dp_debug_live_allocs: the number of device allocations the library holds
+ * at this moment (process-wide), to check that a failed call leaked none.
+ */
+int dp_ctx_set_wait_limit(dp_ctx *ctx, int64_t sleeps);
+int dp_debug_fail_alloc(int32_t k);
+int64_t dp_debug_live_allocs(void);
+
+/*
  * Allocation-free propagation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory -- a solver
  * whose device memory belongs to a pool allocator (a framework's caching

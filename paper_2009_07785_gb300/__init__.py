@@ -38,7 +38,8 @@ SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_ma
            "dp_propagate_persistent",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
            "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
-           "dp_server_destroy")
+           "dp_server_destroy", "dp_ctx_set_wait_limit", "dp_debug_fail_alloc",
+           "dp_debug_live_allocs")
 
 
 class dp_params(C.Structure):
@@ -129,6 +130,12 @@ def lib() -> C.CDLL:
                                         C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float),
                                         C.POINTER(i32)]
     L.dp_propagate_hostloop.restype = C.c_int
+    L.dp_ctx_set_wait_limit.argtypes = [vp, i64]
+    L.dp_ctx_set_wait_limit.restype = C.c_int
+    L.dp_debug_fail_alloc.argtypes = [i32]
+    L.dp_debug_fail_alloc.restype = C.c_int
+    L.dp_debug_live_allocs.argtypes = []
+    L.dp_debug_live_allocs.restype = i64
     L.dp_propagate_noalloc.argtypes = [C.c_int, vp, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp,
                                        C.POINTER(dp_params), vp, vp, C.POINTER(i32),
                                        C.POINTER(i32)]
@@ -219,6 +226,23 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def dp_ctx_set_wait_limit(ctx: Context, sleeps: int) -> None:
+    """Bound (in ~64 ns sleeps; 0 = the default, about 2 s) on a persistent-
+    loop block's wait at a grid barrier before DP_ERR_TIMEOUT."""
+    _check(lib().dp_ctx_set_wait_limit(ctx.handle, int(sleeps)), "dp_ctx_set_wait_limit")
+
+
+def dp_debug_fail_alloc(k: int) -> None:
+    """Test hook: the k-th device allocation of the library from now on fails
+    with DP_ERR_OOM (k = 0 disarms)."""
+    _check(lib().dp_debug_fail_alloc(int(k)), "dp_debug_fail_alloc")
+
+
+def dp_debug_live_allocs() -> int:
+    """Device allocations the library holds now (process-wide)."""
+    return int(lib().dp_debug_live_allocs())
 
 
 def dp_create(device: int = 0, stream=None) -> Context:

@@ -8,6 +8,7 @@
 // without a one-thread driver kernel); an epilogue decodes the bounds; the
 // stream is synchronised once.
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <algorithm>
@@ -19,6 +20,35 @@
 #include "dp_launch.h"
 #include "dp_objects.h"
 #include "../../include/domprop.h"
+
+namespace dp {
+namespace {
+std::atomic<int32_t> g_fail_countdown{0};  // the k-th allocation from now fails (0: none)
+std::atomic<int64_t> g_live_allocs{0};
+}  // namespace
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  int32_t k = g_fail_countdown.load();
+  while (k > 0 && !g_fail_countdown.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 1) {  // this allocation is the one asked to fail
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+void dev_free(void *p) {
+  if (!p) return;
+  cudaFree(p);
+  g_live_allocs.fetch_sub(1);
+}
+
+void arm_alloc_failure(int32_t k) { g_fail_countdown.store(k); }
+int64_t live_allocs() { return g_live_allocs.load(); }
+}  // namespace dp
 
 namespace {
 
@@ -32,7 +62,7 @@ template <typename T>
 int dev_alloc(dp_matrix *mat, T **p, size_t count) {
   void *q = nullptr;
   size_t bytes = sizeof(T) * (count > 0 ? count : 1);
-  cudaError_t e = cudaMalloc(&q, bytes);
+  cudaError_t e = dp::dev_malloc(&q, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA;
@@ -144,6 +174,20 @@ const char *dp_strerror(int code) {
   }
 }
 
+int dp_ctx_set_wait_limit(dp_ctx *ctx, int64_t sleeps) {
+  if (!ctx || sleeps < 0) return DP_ERR_INVALID_ARG;
+  ctx->wait_limit = sleeps == 0 ? dp::kDefaultWaitLimit : (long long)sleeps;
+  return DP_OK;
+}
+
+int dp_debug_fail_alloc(int32_t k) {
+  if (k < 0) return DP_ERR_INVALID_ARG;
+  dp::arm_alloc_failure(k);
+  return DP_OK;
+}
+
+int64_t dp_debug_live_allocs(void) { return dp::live_allocs(); }
+
 int dp_create(dp_ctx **out, int device, void *cuda_stream) {
   if (!out) return DP_ERR_INVALID_ARG;
   *out = nullptr;
@@ -192,7 +236,7 @@ void free_batch(BatchWs *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (void *p : b->allocs) cudaFree(p);
+  for (void *p : b->allocs) dp::dev_free(p);
   if (b->h_ctrl) cudaFreeHost(b->h_ctrl);
   if (b->h_nodes) cudaFreeHost(b->h_nodes);
   delete b;
@@ -207,7 +251,7 @@ void dp_matrix_free(dp_matrix *mat) {
   if (mat->h_inst) cudaFreeHost(mat->h_inst);
   if (mat->exec) cudaGraphExecDestroy(mat->exec);
   if (mat->graph) cudaGraphDestroy(mat->graph);
-  for (void *p : mat->allocs) cudaFree(p);
+  for (void *p : mat->allocs) dp::dev_free(p);
   mat->ctx->live_matrices--;
   delete mat;
 }
@@ -516,6 +560,7 @@ int begin_call(dp_ctx *ctx, dp_matrix *mat, const double *lb, const double *ub,
   hc->tau_rel = p.tau_rel;
   hc->eps_feas = p.eps_feas;
   hc->inf_thr = p.inf_threshold;
+  hc->wait_limit = ctx->wait_limit;
   CUDA_TRY(cudaMemcpyAsync(mat->S.ctrl, hc, sizeof(*hc), cudaMemcpyHostToDevice, st));
   CUDA_TRY(dp::launch_prologue(mat->M, mat->S, mat->vt_ws, m, n, d_lb, d_ub, d_vt, d_lhs, d_rhs,
                                p.eps_int, p.tau_rel, p.inf_threshold, ctx->num_sms, st));
@@ -719,7 +764,7 @@ int track_alloc(std::vector<void *> &allocs, T **p, size_t count, size_t *bytes)
     return DP_OK;
   }
   void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, nb);
+  cudaError_t e = dev_malloc(&q, nb);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA;
@@ -789,7 +834,7 @@ namespace {
 template <typename T>
 int batch_alloc(BatchWs *b, T **p, size_t count) {
   void *q = nullptr;
-  cudaError_t e = cudaMalloc(&q, sizeof(T) * (count > 0 ? count : 1));
+  cudaError_t e = dp::dev_malloc(&q, sizeof(T) * (count > 0 ? count : 1));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : DP_ERR_CUDA;
@@ -819,7 +864,6 @@ int ensure_batch(dp_matrix *mat, int32_t Bp) {
   if (mat->batch) {
     cudaStreamSynchronize(mat->ctx->stream);
     free_batch(mat->batch);
-  if (mat->h_inst) cudaFreeHost(mat->h_inst);
     mat->batch = nullptr;
   }
   BatchWs *b = new (std::nothrow) BatchWs();

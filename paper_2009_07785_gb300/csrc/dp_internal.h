@@ -27,11 +27,22 @@
 
 namespace dp {
 
+// Every device allocation of the library goes through these two (dp_capi.cu):
+// they keep a process-wide count of live allocations and can be told to
+// fail, for the allocation-failure test hook dp_debug_fail_alloc.
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
+void arm_alloc_failure(int32_t k);  // the k-th allocation from now fails; 0 disarms
+int64_t live_allocs();
+
 constexpr int kSliceW = 32;                 // chunks per slice (= warp width)
 constexpr int32_t kLenMask = 0x3FFFFFFF;    // chunk length bits
 constexpr int32_t kExactFlag = 1 << 30;     // row must skip the FP32 screen
 constexpr int32_t kLayoutEll = 0;           // sliced ELL over row chunks
 constexpr int32_t kLayoutMerge = 1;         // merge-path segments over CSR
+// A block of the persistent loop waits at a grid barrier for at most this
+// many 64 ns sleeps (about 2 s) before it records DP_ERR_TIMEOUT and leaves.
+constexpr long long kDefaultWaitLimit = 1ll << 25;
 
 // Current bounds of one variable, as gathered by the round kernels: one
 // 32-byte record, fetched with a single 256-bit load per nonzero.
@@ -100,6 +111,7 @@ struct Ctrl {
   int32_t cont;         // the last round asked for another one
   int32_t pad;
   double eps_int, tau_rel, eps_feas, inf_thr;
+  long long wait_limit;  // persistent loop: sleeps a block waits at a grid barrier
 };
 
 struct DevMatrix {

@@ -647,13 +647,11 @@ k_finish(DevState S, const uint8_t *vartype, int32_t n, cudaGraphConditionalHand
 // single persistent kernel, measured against the graph's WHILE node.
 
 constexpr int kPersistThreads = 256;
-constexpr long long kBarrierSpins = 1ll << 25;  // ~2 s of 64 ns sleeps
-
 // Grid-wide barrier (sense by generation count).  Bounded: a block that
-// waits too long records DP_ERR_TIMEOUT and leaves; every block returns
-// false once an error is recorded.  Cannot deadlock under a cooperative
-// launch, which guarantees that all blocks are resident.
-__device__ __forceinline__ bool grid_sync(const DevState &S) {
+// waits more than `limit` sleeps of 64 ns records DP_ERR_TIMEOUT and leaves;
+// every block returns false once an error is recorded.  Cannot deadlock
+// under a cooperative launch, which guarantees that all blocks are resident.
+__device__ __forceinline__ bool grid_sync(const DevState &S, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned *gen = S.bar + 1;
@@ -666,7 +664,7 @@ __device__ __forceinline__ bool grid_sync(const DevState &S) {
     } else {
       long long it = 0;
       while (*gen == g) {
-        if (++it > kBarrierSpins) {
+        if (++it > limit) {
           atomicExch(&S.ctrl->err, DP_ERR_TIMEOUT);
           break;
         }
@@ -685,6 +683,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2)
 k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
   if (((volatile Ctrl *)S.ctrl)->err) return;  // set before the launch: uniform
   const Ctrl prm = *S.ctrl;  // parameters (constant during the run)
+  const long long lim = prm.wait_limit;
   const float tau_dn = f32_dn(prm.tau_rel), eps_dn = f32_dn(prm.eps_int);
   const int wpb = kPersistThreads / 32;
   const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
@@ -695,22 +694,22 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
       for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, true, kGroupWide>(M, S, sl);
     else
       for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, false, kGroupWide>(M, S, sl);
-    if (!grid_sync(S)) return;
+    if (!grid_sync(S, lim)) return;
     if (M.nsplit_rows > 0) {
       for (int w = gw; w < M.nsplit_rows; w += nw) combine_rows<false>(M, S, w);
-      if (!grid_sync(S)) return;
+      if (!grid_sync(S, lim)) return;
       for (int sl = gw; sl < M.nslices_split; sl += nw) cand_split_slice(M, S, sl);
-      if (!grid_sync(S)) return;
+      if (!grid_sync(S, lim)) return;
     }
     const int32_t cnt = ((volatile Ctrl *)S.ctrl)->qcount;
     for (int64_t e = gt; e < cnt; e += nt) cand_entries<false, 1>(M, S, prm, e, nt, cnt);
-    if (!grid_sync(S)) return;
+    if (!grid_sync(S, lim)) return;
     for (int64_t w0 = (gt >> 5) * kFinishWords; w0 < ((int64_t)M.n + 31) >> 5;
          w0 += (nt >> 5) * kFinishWords)
       finish_words<false>(S, vartype, w0, ((int64_t)M.n + 31) >> 5, prm.eps_feas, tau_dn, eps_dn);
-    if (!grid_sync(S)) return;
+    if (!grid_sync(S, lim)) return;
     if (blockIdx.x == 0) decide_round<false>(S);
-    if (!grid_sync(S)) return;
+    if (!grid_sync(S, lim)) return;
     if (!((volatile Ctrl *)S.ctrl)->cont) return;
   }
 }

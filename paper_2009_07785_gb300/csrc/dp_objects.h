@@ -14,6 +14,7 @@ struct dp_ctx {
   bool own_stream = false;
   dp::Ctrl *h_ctrl = nullptr;  // pinned mirror of the device control block
   int live_matrices = 0;
+  long long wait_limit = dp::kDefaultWaitLimit;  // grid-barrier wait of the persistent loop
 };
 
 struct dp_matrix {

@@ -129,7 +129,7 @@ void free_workspace(Lane &L) {
   if (L.ev_round) cudaEventDestroy(L.ev_round);
   if (L.ev_extract) cudaEventDestroy(L.ev_extract);
   if (L.stream) cudaStreamDestroy(L.stream);
-  for (void *p : L.dev_allocs) cudaFree(p);
+  for (void *p : L.dev_allocs) dp::dev_free(p);
   for (void *p : L.host_allocs) cudaFreeHost(p);
   L.dev_allocs.clear();
   L.host_allocs.clear();
@@ -148,7 +148,7 @@ size_t lane_bytes(const Lane &L, int32_t Bp) {
 template <typename T>
 int lane_dev(Lane &L, T **p, size_t count) {
   void *q = nullptr;
-  if (cudaMalloc(&q, sizeof(T) * (count > 0 ? count : 1)) != cudaSuccess) {
+  if (dp::dev_malloc(&q, sizeof(T) * (count > 0 ? count : 1)) != cudaSuccess) {
     cudaGetLastError();
     return DP_ERR_OOM;
   }
@@ -518,16 +518,16 @@ int dp_server_add_matrix(dp_server *s, const dp_matrix *mat, const uint8_t *vart
   L->m = m;
   L->n = n;
   if (cudaSetDevice(s->ctx->device) != cudaSuccess ||
-      cudaMalloc(&L->d_lhs, 8 * (size_t)(m > 0 ? m : 1)) != cudaSuccess ||
-      cudaMalloc(&L->d_rhs, 8 * (size_t)(m > 0 ? m : 1)) != cudaSuccess ||
-      cudaMalloc(&L->d_vt, (size_t)(n > 0 ? n : 1)) != cudaSuccess ||
+      dp::dev_malloc((void **)&L->d_lhs, 8 * (size_t)(m > 0 ? m : 1)) != cudaSuccess ||
+      dp::dev_malloc((void **)&L->d_rhs, 8 * (size_t)(m > 0 ? m : 1)) != cudaSuccess ||
+      dp::dev_malloc((void **)&L->d_vt, (size_t)(n > 0 ? n : 1)) != cudaSuccess ||
       (m > 0 && cudaMemcpy(L->d_lhs, lhs, 8 * (size_t)m, cudaMemcpyDefault) != cudaSuccess) ||
       (m > 0 && cudaMemcpy(L->d_rhs, rhs, 8 * (size_t)m, cudaMemcpyDefault) != cudaSuccess) ||
       (n > 0 && cudaMemcpy(L->d_vt, vartype, (size_t)n, cudaMemcpyDefault) != cudaSuccess)) {
     cudaGetLastError();
-    cudaFree(L->d_lhs);
-    cudaFree(L->d_rhs);
-    cudaFree(L->d_vt);
+    dp::dev_free(L->d_lhs);
+    dp::dev_free(L->d_rhs);
+    dp::dev_free(L->d_vt);
     delete L;
     return DP_ERR_CUDA;
   }
@@ -612,9 +612,9 @@ int dp_server_destroy(dp_server *s) {
   for (Lane *L : s->lanes) {
     if (L->stream) cudaStreamSynchronize(L->stream);
     free_workspace(*L);
-    cudaFree(L->d_lhs);
-    cudaFree(L->d_rhs);
-    cudaFree(L->d_vt);
+    dp::dev_free(L->d_lhs);
+    dp::dev_free(L->d_rhs);
+    dp::dev_free(L->d_vt);
     delete L;
   }
   delete s;

@@ -118,12 +118,18 @@ def test_tiny_split_rows(gpu, orc, chunk):
         replay(dp, ctx, mat, inst, orc)
 
 
+# replayed decisions the oracle flags as ties may go either way; a few per
+# workload are expected with fractional data, many would point at a bug
+TIE_BUDGET = 20
+
+
 def test_medium_scaled(gpu, orc):
     dp, ctx = gpu
     inst = synth.medium(scale=0.1)
     with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
         assert mat.info()["split_rows"] > 0
-        replay(dp, ctx, mat, inst, orc)
+        _, ties = replay(dp, ctx, mat, inst, orc)
+        assert ties <= TIE_BUDGET
         check_full(dp, ctx, mat, inst, orc, exact=False)
 
 
@@ -132,7 +138,8 @@ def test_large_scaled(gpu, orc):
     inst = synth.large(scale=0.02)
     with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
         assert mat.info()["split_rows"] > 0
-        replay(dp, ctx, mat, inst, orc)
+        _, ties = replay(dp, ctx, mat, inst, orc)
+        assert ties <= TIE_BUDGET
         check_full(dp, ctx, mat, inst, orc, exact=False)
 
 
@@ -169,7 +176,8 @@ def test_large_scaled_side_ordered(gpu, orc):
     inst = synth.large(scale=0.02)
     with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val,
                    lhs=inst.lhs, rhs=inst.rhs) as mat:
-        replay(dp, ctx, mat, inst, orc)
+        _, ties = replay(dp, ctx, mat, inst, orc)
+        assert ties <= TIE_BUDGET
         check_full(dp, ctx, mat, inst, orc, exact=False)
 
 
