@@ -114,6 +114,11 @@ def parse():
     ap.add_argument("--workload", choices=["large", "medium", "tiny"], default="large")
     ap.add_argument("--chunk", type=int, default=0,
                     help="row split length (0: chosen by the autotuner)")
+    ap.add_argument("--round-warps", type=int, default=8, choices=[4, 8],
+                    help="warps per block of the round kernels when --chunk is given")
+    ap.add_argument("--per-round", action="store_true",
+                    help="only print per-round kernel times of one propagation (host loop, "
+                         "one round per call from the previous round's bounds)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (chunk 256, 8 warps per block)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -385,6 +390,25 @@ def run_reference(args):
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def per_round_times(dp, ctx, mat, d_in, max_rounds=100):
+    """Kernel times of every round of one propagation: each round is one
+    host-loop call with max_rounds = 1 from the bounds the previous call
+    returned (the same rounds as one call to the fixed point)."""
+    p1 = dp.dp_params_default(max_rounds=1)
+    for _ in range(2):  # warm-up
+        dp.dp_propagate_hostloop(ctx, mat, *d_in, params=p1)
+    lb, ub = d_in[0].clone(), d_in[1].clone()
+    rows = []
+    for r in range(1, max_rounds + 1):
+        res = dp.dp_propagate_hostloop(ctx, mat, lb, ub, *d_in[2:], params=p1, timing=True)
+        rows.append({"round": r, **{k: round(res.kernel_ms[i] * 1e3, 1)
+                                    for i, k in enumerate(dp.KERNELS)}})
+        lb, ub = res.lb.clone(), res.ub.clone()
+        if res.status != dp.DP_CAP_HIT or res.infeasible:
+            break
+    return rows
 
 
 def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3, chunk=0):
@@ -683,7 +707,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = dp.Context(local, stream)
     tune = None
-    chunk, warps = args.chunk, 8
+    chunk, warps = args.chunk, args.round_warps
     if not args.no_autotune and not args.chunk:
         t0 = time.perf_counter()
         tune = dp.dp_autotune(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val, inst.lb,
@@ -699,6 +723,13 @@ def run_ours(args):
     mat.set_compression(False)
     info = mat.info()
     d_in = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in inst.problem()]
+    if args.per_round:
+        print(json.dumps({"per_round": per_round_times(dp, ctx, mat, d_in),
+                          "config": {**describe(inst), "chunk": chunk or 256,
+                                     "round_warps": warps}}))
+        mat.close()
+        ctx.close()
+        return 0
     d_lb = torch.empty(inst.n, dtype=torch.float64, device="cuda")
     d_ub = torch.empty_like(d_lb)
     torch.cuda.synchronize()

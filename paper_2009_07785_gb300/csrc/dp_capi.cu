@@ -136,10 +136,48 @@ int build_loop_graph(Body body, cudaGraph_t *graph_out, cudaGraphExec_t *exec_ou
   return DP_OK;
 }
 
+// The variables' records are gathered once per nonzero and round while the
+// matrix streams past them; the round graph's kernels ask L2 to keep the
+// records resident (an access-policy window with the persisting property,
+// within the L2 set-aside of this context) so that the stream does not
+// evict them.  Best effort: a device or driver that refuses leaves the
+// ordinary policy in place.
+void l2_keep_records(const dp_matrix *mat, cudaStream_t cs) {
+  const size_t bytes = sizeof(dp::VarRec) * (size_t)(mat->M.n > 0 ? mat->M.n : 1);
+  int max_persist = 0, max_window = 0;
+  const int dev = mat->ctx->device;
+  if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev) !=
+          cudaSuccess ||
+      max_persist <= 0 || max_window <= 0) {
+    cudaGetLastError();
+    return;
+  }
+  size_t cur = 0;
+  cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+  const size_t want = bytes < (size_t)max_persist ? bytes : (size_t)max_persist;
+  if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+  cudaStreamAttrValue v = {};
+  v.accessPolicyWindow.base_ptr = mat->S.rec;
+  v.accessPolicyWindow.num_bytes = bytes < (size_t)max_window ? bytes : (size_t)max_window;
+  const double ratio = (double)cur / (double)v.accessPolicyWindow.num_bytes;
+  v.accessPolicyWindow.hitRatio = (float)(ratio < 1.0 ? ratio : 1.0);
+  v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  if (cudaStreamSetAttribute(cs, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess)
+    cudaGetLastError();
+}
+
 int build_graph(dp_matrix *mat) {
   const int sms = mat->ctx->num_sms;
   return build_loop_graph(
       [mat, sms](cudaGraphConditionalHandle h, cudaStream_t cs) {
+        l2_keep_records(mat, cs);
         return dp::launch_round_body(mat->M, mat->S, mat->vt_ws, h, sms, cs);
       },
       &mat->graph, &mat->exec);
