@@ -824,10 +824,16 @@ def run_ours(args):
     b_round, b_finish = algorithmic_bytes(inst)
     peak, peak_kind = peaks()
     ach = b_round / (kms["round"] * 1e-3) / 1e9
+    floor_us = dp.dp_matrix_access_floor(ctx, mat, 5)
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "traffic": ncu_traffic(chunk or 256),
             "kernel": "k_round", "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": b_round, "avg_launch_us": round(kms["round"] * 1e3, 2)}
+            "algorithmic_bytes_per_launch": b_round, "avg_launch_us": round(kms["round"] * 1e3, 2),
+            # the same matrix's memory accesses of one round without the
+            # arithmetic (every value and column streamed, every record
+            # gathered): the floor the access pattern sets on k_round
+            "access_floor_us": round(floor_us, 2),
+            "access_floor_frac": round(b_round / (floor_us * 1e-6) / 1e9 / peak, 4)}
 
     # end to end through the public call with pinned host buffers
     e2e = None

@@ -259,6 +259,20 @@ int dp_matrix_info(const dp_matrix *mat, int32_t *m, int32_t *n,
                    int64_t *nnz, int64_t *padded_slots, int32_t *split_rows);
 
 /*
+ * Measurement, not propagation (the paper's roofline analysis, Sec. 4.4,
+ * asks what bounds a round; this measures it on the loaded matrix): times
+ * `reps` launches (after one warm-up) of a kernel that makes the memory
+ * accesses of one round's activity pass on this matrix's layout and launch
+ * shape -- every value and column streamed, every nonzero's 32-byte
+ * variable record gathered -- and does none of its arithmetic.  *us gets the
+ * fastest launch in microseconds: the floor that the round's memory traffic
+ * sets.  The records need not hold bounds (their contents are not used).
+ * Synchronises the context's stream.  Sliced layout only.  Returns DP_OK,
+ * DP_ERR_INVALID_ARG or DP_ERR_CUDA.
+ */
+int dp_matrix_access_floor(dp_ctx *ctx, const dp_matrix *mat, int32_t reps, float *us);
+
+/*
  * Propagates one problem over a loaded matrix (Alg. 2, round-synchronous).
  * Inputs (host or device, all binary64 unless noted; not modified):
  *   lb[n], ub[n]      variable bounds

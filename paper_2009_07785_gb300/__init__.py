@@ -39,7 +39,7 @@ SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_ma
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
            "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
            "dp_server_destroy", "dp_ctx_set_wait_limit", "dp_debug_fail_alloc",
-           "dp_debug_live_allocs")
+           "dp_debug_live_allocs", "dp_matrix_access_floor")
 
 
 class dp_params(C.Structure):
@@ -130,6 +130,8 @@ def lib() -> C.CDLL:
                                         C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float),
                                         C.POINTER(i32)]
     L.dp_propagate_hostloop.restype = C.c_int
+    L.dp_matrix_access_floor.argtypes = [vp, vp, i32, C.POINTER(C.c_float)]
+    L.dp_matrix_access_floor.restype = C.c_int
     L.dp_ctx_set_wait_limit.argtypes = [vp, i64]
     L.dp_ctx_set_wait_limit.restype = C.c_int
     L.dp_debug_fail_alloc.argtypes = [i32]
@@ -226,6 +228,15 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def dp_matrix_access_floor(ctx: Context, mat: Matrix, reps: int = 5) -> float:
+    """Microseconds of the round's memory access pattern on this matrix
+    without its arithmetic (fastest of `reps` launches)."""
+    us = C.c_float()
+    _check(lib().dp_matrix_access_floor(ctx.handle, mat.handle, int(reps), C.byref(us)),
+           "dp_matrix_access_floor")
+    return float(us.value)
 
 
 def dp_ctx_set_wait_limit(ctx: Context, sleeps: int) -> None:

@@ -314,6 +314,62 @@ k_round(DevMatrix M, DevState S) {
   round_slice<kMulti, kVal8, kMulti ? kGroupWide : kGroup>(M, S, slice);
 }
 
+// ------------------------------------------------------------- k_floor --
+//
+// The memory access pattern of k_round's activity pass alone, on the same
+// layout and in the same launch shape: every slot's value and column
+// streamed, every nonzero's 32-byte record gathered, no arithmetic beyond an
+// integer fold that keeps the loads alive.  Its time is the floor that the
+// round kernel's memory traffic sets on this matrix (a measurement, not part
+// of propagation).
+template <int kRoundWarps>
+__global__ void __launch_bounds__(kRoundWarps * 32, kRoundWarpsPerSM / kRoundWarps)
+k_floor(DevMatrix M, DevState S, unsigned *sink) {
+  const int slice = blockIdx.x * kRoundWarps + (threadIdx.x >> 5);
+  if (slice >= M.nslices) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)slice * kSliceW + lane;
+  const int32_t len = M.chunk_len[c] & kLenMask;
+  const int64_t vo = M.slice_off[slice] + lane;
+  unsigned acc = 0u;
+  for (int k = 0; k < len; k += kGroup) {
+    double a[kGroup];
+    int32_t j[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      a[u] = 0.0;
+      j[u] = 0;
+      if (k + u < len) {
+        a[u] = __ldcs(M.val + vo + (int64_t)(k + u) * kSliceW);
+        j[u] = __ldcs(M.col + vo + (int64_t)(k + u) * kSliceW);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      if (k + u < len) {
+        double L, U;
+        float WU, WL;
+        uint32_t fl;
+        ld_rec(S.rec + j[u], L, U, WU, WL, fl);
+        acc ^= (unsigned)__double_as_longlong(L) ^ (unsigned)__double_as_longlong(a[u]) ^
+               __float_as_uint(WU) ^ fl;
+      }
+    }
+  }
+  if (acc == 0x9E3779B9u) *sink = acc;  // practically never: keeps the loads
+}
+
+cudaError_t launch_access_floor(const DevMatrix &M, const DevState &S, unsigned *sink,
+                                cudaStream_t st) {
+  if (M.layout != kLayoutEll) return cudaErrorInvalidValue;
+  const int w = M.round_warps == 4 ? 4 : 8;
+  int nb = (M.nslices + w - 1) / w;
+  if (nb < 1) nb = 1;
+  if (w == 4) k_floor<4><<<nb, 4 * 32, 0, st>>>(M, S, sink);
+  else k_floor<8><<<nb, 8 * 32, 0, st>>>(M, S, sink);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ k_combine --
 
 constexpr int kCombineWarps = 8;

@@ -29,6 +29,11 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S,
                                  int use_cond, int num_sms, cudaStream_t st,
                                  cudaEvent_t *ev);
 
+// One launch of the round's memory access pattern without its arithmetic
+// (k_floor; sliced layout only) on `st`.
+cudaError_t launch_access_floor(const DevMatrix &M, const DevState &S, unsigned *sink,
+                                cudaStream_t st);
+
 // The whole round loop as one cooperative (persistent) launch on `st`
 // (single problems only).
 cudaError_t launch_persistent(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
