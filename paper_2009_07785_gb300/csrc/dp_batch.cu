@@ -127,38 +127,6 @@ __device__ __forceinline__ void note_nodes(uint32_t *bits, int g, bool h) {
   if ((threadIdx.x & 31) == 0 && (bits[g] & m) != m) atomicOr(&bits[g], m);
 }
 
-// Entries improved in a round are staged per warp in shared memory and
-// appended to the global dirty list in bulk, one counter atomic per
-// kStage entries rather than one per warp instruction.
-constexpr int kStage = 128;
-
-struct DirtyStage {
-  uint32_t *buf;  // this warp's shared-memory buffer
-  int n;          // staged entries (warp-uniform)
-};
-
-__device__ __forceinline__ void stage_flush(DirtyStage &st, uint32_t *list, int32_t *count) {
-  __syncwarp();
-  if (st.n == 0) return;
-  const int lane = threadIdx.x & 31;
-  int base = 0;
-  if (lane == 0) base = atomicAdd(count, st.n);
-  base = __shfl_sync(kFull, base, 0);
-  for (int i = lane; i < st.n; i += 32) list[base + i] = st.buf[i];
-  __syncwarp();
-  st.n = 0;
-}
-
-__device__ __forceinline__ void stage_push(DirtyStage &st, bool h, uint32_t e, uint32_t *list,
-                                           int32_t *count) {
-  const unsigned m = __ballot_sync(kFull, h);
-  if (m == 0u) return;
-  if (st.n + 32 > kStage) stage_flush(st, list, count);
-  const int lane = threadIdx.x & 31;
-  if (h) st.buf[st.n + __popc(m & ((1u << lane) - 1u))] = e;
-  st.n += __popc(m);
-}
-
 // Activity of one chunk for this lane's node (Def. 1 / Eq. 2a, 2b; an
 // infinite contribution is counted, not summed, Sec. 3.4), plus the
 // largest binary32 screen value of each needed side.  The sums are one
@@ -252,30 +220,25 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
 
 // Candidates of one nonzero for one node from the sides that survived the
 // screen (side_candidate), applied with order-preserving 64-bit atomics to
-// the node's next state kp = {lower key, upper key}.  Returns whether this
-// lane made the first improvement of the entry in this round (the atomic saw
-// the start-of-round key), which puts the entry on the dirty list exactly
-// once per side.
+// the node's next state kp = {lower key, upper key}; nothing waits for the
+// atomics.  Returns whether a candidate was applied (it improves the
+// round's starting bound, so the entry changes this round).
 __device__ __forceinline__ bool bnnz_candidates(double a, bool isint, double L, double U,
                                                 unsigned sides, const RowView &rv,
                                                 const BParams &P, long long *kp) {
-  bool first = false;
+  bool applied = false;
   auto apply = [&](const SideCand &c) {
     if (!c.apply) return;
     const long long nk = key_of(c.v);
-    if (c.upper) {
-      const long long old = atomicMin(&kp[1], nk);
-      first |= (old == key_of(U) && nk < old);
-    } else {
-      const long long old = atomicMax(&kp[0], nk);
-      first |= (old == key_of(L) && nk > old);
-    }
+    if (c.upper) atomicMin(&kp[1], nk);
+    else atomicMax(&kp[0], nk);
+    applied = true;
   };
   apply(side_candidate(a, L, U, isint, (sides & 1u) != 0u, rv, P.eps_int, P.tau_rel,
                        P.inf_thr));
   if (sides == 3u)
     apply(side_candidate(a, L, U, isint, false, rv, P.eps_int, P.tau_rel, P.inf_thr));
-  return first;
+  return applied;
 }
 
 // Nonzero-node pairs that survived the screen wait in a per-warp buffer and
@@ -297,16 +260,16 @@ struct PairQueue {
   int n;         // buffered pairs (warp-uniform)
 };
 
-// Evaluates pairs [from, from + count) of the buffer, count <= 32.  All 32
-// lanes call.
+// Evaluates pairs [from, from + count) of the buffer, count <= 32, and
+// marks the entries they change in the round's change mask chg_next (one
+// atomic per mask word among the lanes).  All 32 lanes call.
 __device__ __forceinline__ void eval_pairs(PairQueue &pq, int from, int count,
                                            const DevMatrix &M, const BatchState &S,
-                                           const BParams &P, DirtyStage &st, uint32_t *dirty,
-                                           int32_t *ndirty) {
+                                           const BParams &P, uint32_t *chg_next) {
   __syncwarp();
   const int lane = threadIdx.x & 31;
-  bool first = false;
-  uint32_t e = 0u;
+  unsigned long long widx = ~0ull;
+  uint32_t bit = 0u;
   if (lane < count) {
     const int q = from + lane;
     const PairBuf &B = *pq.buf;
@@ -322,56 +285,83 @@ __device__ __forceinline__ void eval_pairs(PairQueue &pq, int from, int count,
     rv.rhs = S.rhs[row];
     const double a = __ldg(M.val + off);
     const int32_t j = __ldg(M.col + off);
-    e = (uint32_t)((int64_t)j * P.Bp + node);
+    const int64_t e = (int64_t)j * P.Bp + node;
     const double2 b = ld_bounds(S.cur + e);
     const bool isint = __ldg(S.vt + j) != 0;
-    first = bnnz_candidates(a, isint, b.x, b.y, info & 3u, rv, P, S.nkey + 2 * (int64_t)e);
+    if (bnnz_candidates(a, isint, b.x, b.y, info & 3u, rv, P, S.nkey + 2 * e)) {
+      widx = (unsigned long long)j * P.Gs + (node >> 5);
+      bit = 1u << (node & 31);
+    }
   }
+  const unsigned peers = __match_any_sync(kFull, widx);
+  const uint32_t bits = __reduce_or_sync(peers, bit);
+  if (bit != 0u && lane == __ffs(peers) - 1) atomicOr(&chg_next[widx], bits);
   __syncwarp();
-  stage_push(st, first, e, dirty, ndirty);
 }
 
 // Candidates of one chunk for this lane's node; `on` = the node processes
 // the chunk and its row may yield an accepted candidate.  The screen is
 // recomputed from the bounds (binary32 and integer work, which overlaps
 // with the loads), so binary64 candidate work runs only for nonzeros that
-// can tighten.  All 32 lanes call.
+// can tighten.  Four nonzeros are screened per step, their loads in flight
+// together; the survivors then enter the pair buffer in CSR order.  All 32
+// lanes call.
 __device__ __forceinline__ void chunk_candidates(const DevMatrix &M, const BatchState &S,
                                                  int64_t base, int len, int node, bool on,
                                                  int32_t row, const RowView &rv,
                                                  const BParams &P, PairQueue &pq,
-                                                 DirtyStage &st, uint32_t *dirty,
-                                                 int32_t *ndirty) {
+                                                 uint32_t *chg_next) {
   const int lane = threadIdx.x & 31;
   const double *vp = M.val + base;
   const int32_t *cp = M.col + base;
   const uint32_t ctx = ((uint32_t)node << 4) | (rv.maxinf == 0 ? 8u : 0u) |
                        (rv.mininf == 0 ? 4u : 0u);
-  for (int k = 0; k < len; ++k) {
-    const double a = __ldg(vp + (int64_t)k * kSliceW);
-    const int32_t j = __ldg(cp + (int64_t)k * kSliceW);
-    unsigned sides = 0u;
+  const double2 *bp = S.cur + node;
+  const float2 *wp = S.wid + node;
+  for (int k0 = 0; k0 < len; k0 += 4) {
+    const int nk = min(4, len - k0);
+    // bits 2u, 2u+1: the surviving sides of nonzero k0 + u
+    unsigned sides4 = 0u;
     if (on) {
-      const int64_t e = (int64_t)j * P.Bp + node;
-      const double2 b = ld_bounds(S.cur + e);
-      const float2 w = ld_widths(S.wid + e);
-      sides = nnz_sides(a, b.x, b.y, w.x, w.y, rv);
+      double a[4];
+      int32_t j[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + (u < nk ? u : 0);
+        a[u] = __ldg(vp + (int64_t)k * kSliceW);
+        j[u] = __ldg(cp + (int64_t)k * kSliceW);
+      }
+      double2 b[4];
+      float2 w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        b[u] = ld_bounds(bp + (int64_t)j[u] * P.Bp);
+        w[u] = ld_widths(wp + (int64_t)j[u] * P.Bp);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < nk) sides4 |= nnz_sides(a[u], b[u].x, b[u].y, w[u].x, w[u].y, rv) << (2 * u);
     }
-    const unsigned m = __ballot_sync(kFull, sides != 0u);
-    if (m == 0u) continue;
-    if (sides) {
-      const int q = pq.n + __popc(m & ((1u << lane) - 1u));
-      PairBuf &B = *pq.buf;
-      B.off[q] = (uint32_t)(base + (int64_t)k * kSliceW);
-      B.info[q] = ctx | sides;
-      B.row[q] = row;
-      B.minfin[q] = rv.minfin;
-      B.maxfin[q] = rv.maxfin;
-    }
-    pq.n += __popc(m);
-    if (pq.n >= 32) {
-      pq.n -= 32;
-      eval_pairs(pq, pq.n, 32, M, S, P, st, dirty, ndirty);
+    if (__ballot_sync(kFull, sides4 != 0u) == 0u) continue;
+#pragma unroll 1
+    for (int u = 0; u < nk; ++u) {
+      const unsigned sides = (sides4 >> (2 * u)) & 3u;
+      const unsigned m = __ballot_sync(kFull, sides != 0u);
+      if (m == 0u) continue;
+      if (sides) {
+        const int q = pq.n + __popc(m & ((1u << lane) - 1u));
+        PairBuf &B = *pq.buf;
+        B.off[q] = (uint32_t)(base + (int64_t)(k0 + u) * kSliceW);
+        B.info[q] = ctx | sides;
+        B.row[q] = row;
+        B.minfin[q] = rv.minfin;
+        B.maxfin[q] = rv.maxfin;
+      }
+      pq.n += __popc(m);
+      if (pq.n >= 32) {
+        pq.n -= 32;
+        eval_pairs(pq, pq.n, 32, M, S, P, chg_next);
+      }
     }
   }
 }
@@ -379,10 +369,9 @@ __device__ __forceinline__ void chunk_candidates(const DevMatrix &M, const Batch
 // Evaluates what is left in the pair buffer (end of a warp's work).
 __device__ __forceinline__ void drain_pairs(PairQueue &pq, const DevMatrix &M,
                                             const BatchState &S, const BParams &P,
-                                            DirtyStage &st, uint32_t *dirty, int32_t *ndirty) {
-  if (pq.n > 0) eval_pairs(pq, 0, pq.n, M, S, P, st, dirty, ndirty);
+                                            uint32_t *chg_next) {
+  if (pq.n > 0) eval_pairs(pq, 0, pq.n, M, S, P, chg_next);
   pq.n = 0;
-  stage_flush(st, dirty, ndirty);
 }
 
 // ------------------------------------------------------------- k_bmark --
@@ -496,7 +485,10 @@ __global__ void __launch_bounds__(kThreads) k_bmark_split(DevMatrix M, BatchStat
 
 // -------------------------------------------------------------- k_bact --
 
-__global__ void __launch_bounds__(kActWarps * 32, 3) k_bact(DevMatrix M, BatchState S) {
+// Four blocks of eight warps per SM (64 registers, a few spilled): the
+// kernel waits on gathers, and 32 resident warps hide more of that latency
+// than 24 warps without spills do (7% faster on a dense first round).
+__global__ void __launch_bounds__(kActWarps * 32, 4) k_bact(DevMatrix M, BatchState S) {
   BCtrl *ctrl = S.ctrl;
   const BParams P = load_params(ctrl);
   if (P.err) return;
@@ -514,10 +506,9 @@ __global__ void __launch_bounds__(kActWarps * 32, 3) k_bact(DevMatrix M, BatchSt
   const int excl = incl - cnt;
   const int64_t split_slots = (int64_t)M.nslices_split * kSliceW;
   const int nw = gridDim.x * kActWarps;
-  __shared__ uint32_t s_stage[kActWarps][kStage];
   __shared__ PairBuf s_pairs[kActWarps];
-  DirtyStage st{s_stage[threadIdx.x >> 5], 0};
   PairQueue pq{&s_pairs[threadIdx.x >> 5], 0};
+  uint32_t *chg_next = S.chg[p ^ 1];
   for (int it = blockIdx.x * kActWarps + (threadIdx.x >> 5); it < total; it += nw) {
     const int g = __popc(__ballot_sync(kFull, lane < P.G && it >= incl));
     const int off = __shfl_sync(kFull, excl, g);
@@ -556,10 +547,9 @@ __global__ void __launch_bounds__(kActWarps * 32, 3) k_bact(DevMatrix M, BatchSt
     note_nodes(S.inf_bits, g, on && infeas);
     const bool go = on && rv.act != 0;
     if (!__any_sync(kFull, go)) continue;
-    chunk_candidates(M, S, base, len, node, go, row, rv, P, pq, st, S.dirty[p],
-                     &ctrl->ndirty[p]);
+    chunk_candidates(M, S, base, len, node, go, row, rv, P, pq, chg_next);
   }
-  drain_pairs(pq, M, S, P, st, S.dirty[p], &ctrl->ndirty[p]);
+  drain_pairs(pq, M, S, P, chg_next);
 }
 
 // ---------------------------------------------------------- split rows --
@@ -631,10 +621,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchS
   const int lane = threadIdx.x & 31;
   const int64_t pairs = (int64_t)M.nslices_split * kSliceW * P.G;
   const int nw = gridDim.x * (blockDim.x >> 5);
-  __shared__ uint32_t s_stage[kThreads / 32][kStage];
   __shared__ PairBuf s_pairs[kThreads / 32];
-  DirtyStage st{s_stage[threadIdx.x >> 5], 0};
   PairQueue pq{&s_pairs[threadIdx.x >> 5], 0};
+  uint32_t *chg_next = S.chg[p ^ 1];
   for (int64_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < pairs; w += nw) {
     const int64_t cs = w / P.G;
     const int g = (int)(w % P.G);
@@ -659,20 +648,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchS
     rv.exact = (lenf & kExactFlag) ? 1 : 0;
     rv.act = on ? 1 : 0;
     const int64_t base = M.slice_off[cs / kSliceW] + (cs % kSliceW);
-    chunk_candidates(M, S, base, lenf & kLenMask, node, on, row, rv, P, pq, st, S.dirty[p],
-                     &ctrl->ndirty[p]);
+    chunk_candidates(M, S, base, lenf & kLenMask, node, on, row, rv, P, pq, chg_next);
   }
-  drain_pairs(pq, M, S, P, st, S.dirty[p], &ctrl->ndirty[p]);
+  drain_pairs(pq, M, S, P, chg_next);
 }
 
 // ----------------------------------------------------------- k_bfinish --
 
 // Commits the entries improved this round (the next state becomes the
-// current one), tests them for crossing bounds (Sec. 1.1, remark after
-// Step 3), and records which (variable, node) pairs changed; clears the
-// change masks of the previous round.  The last block to arrive counts the
-// round for every live node, ends the nodes that stopped (no change,
-// infeasible, or the cap) and sets the WHILE condition.
+// current one) and tests them for crossing bounds (Sec. 1.1, remark after
+// Step 3).  The entries are those marked in this round's change mask, which
+// the candidate kernels set; a warp reads 32 consecutive mask words and
+// commits each nonzero word with one lane per node of its group, so that the
+// state is read and written in contiguous runs.  The previous round's mask
+// (read by this round's marking) is cleared for reuse.  The last block to
+// arrive counts the round for every live node, ends the nodes that stopped
+// (no change, infeasible, or the cap) and sets the WHILE condition.
 __global__ void __launch_bounds__(kThreads)
 k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_cond) {
   BCtrl *ctrl = S.ctrl;
@@ -687,44 +678,60 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
   }
   __syncthreads();
   if (!P.err) {
-    const int32_t nd = ctrl->ndirty[p];
-    const uint32_t *list = S.dirty[p];
-    uint32_t *chg_next = S.chg[p ^ 1];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform trip count: lanes of one warp merge their change-mask
-    // updates of the same (variable, group) word into one atomic
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nd;
-         i0 += stride) {
-      const int64_t i = i0 + lane;
-      const bool valid = i < nd;
-      unsigned long long widx = ~0ull;
-      uint32_t bit = 0u;
-      if (valid) {
-        const uint32_t e = list[i];
-        const uint32_t j = e / (uint32_t)P.Bp, node = e % (uint32_t)P.Bp;
-        const longlong2 kk = reinterpret_cast<const longlong2 *>(S.nkey)[e];
-        const double L = val_of_key(kk.x), U = val_of_key(kk.y);
-        put_entry(S, e, L, U, S.vt[j] != 0, P.tau_dn, P.eps_dn);
-        if (kk.x > kk.y) {  // L > U in key order: test the crossing exactly
-          const bool cross = S.vt[j] ? (L > U) : (L > U + P.eps_feas * d_max1abs(U));
-          if (cross) atomicOr(&s_inf[node >> 5], 1u << (node & 31));
-        }
-        widx = (unsigned long long)j * P.Gs + (node >> 5);
-        bit = 1u << (node & 31);
-        atomicOr(&s_chg[node >> 5], bit);
-      }
-      const unsigned peers = __match_any_sync(kFull, widx);
-      const uint32_t bits = __reduce_or_sync(peers, bit);
-      if (valid && lane == __ffs(peers) - 1) atomicOr(&chg_next[widx], bits);
-    }
-    // clear the change masks that the previous round's entries set
-    const int32_t np = ctrl->ndirty[p ^ 1];
-    const uint32_t *prev = S.dirty[p ^ 1];
+    const uint32_t *chg_next = S.chg[p ^ 1];
     uint32_t *chg_cur = S.chg[p];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
-      const uint32_t e = prev[i];
-      const uint32_t j = e / (uint32_t)P.Bp, node = e % (uint32_t)P.Bp;
-      chg_cur[(int64_t)j * P.Gs + (node >> 5)] = 0u;
+    const int64_t words = (int64_t)n * P.Gs;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;  // 32 words per warp
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < words;
+         w0 += wstride) {
+      uint32_t c = 0u;
+      if (w0 + lane < words) {
+        c = chg_next[w0 + lane];
+        if (chg_cur[w0 + lane] != 0u) chg_cur[w0 + lane] = 0u;
+      }
+      unsigned nz = __ballot_sync(kFull, c != 0u);
+      while (nz != 0u) {
+        // up to four nonzero words per step, their loads in flight together
+        int k[4];
+        uint32_t wd[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          k[u] = nz != 0u ? __ffs(nz) - 1 : 0;
+          const uint32_t v = __shfl_sync(kFull, c, k[u]);
+          wd[u] = nz != 0u ? v : 0u;
+          nz &= nz - 1u;
+        }
+        longlong2 kk[4];
+        bool isint[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t w = w0 + k[u];
+          const int64_t j = w / P.Gs;
+          const int node = (int)(w % P.Gs) * 32 + lane;
+          kk[u] = make_longlong2(0, 0);
+          isint[u] = false;
+          if ((wd[u] >> lane) & 1u) {
+            kk[u] = reinterpret_cast<const longlong2 *>(S.nkey)[j * P.Bp + node];
+            isint[u] = S.vt[j] != 0;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t w = w0 + k[u];
+          const int64_t j = w / P.Gs;
+          const int g = (int)(w % P.Gs);
+          const int node = g * 32 + lane;
+          if ((wd[u] >> lane) & 1u) {
+            const double L = val_of_key(kk[u].x), U = val_of_key(kk[u].y);
+            put_entry(S, j * P.Bp + node, L, U, isint[u], P.tau_dn, P.eps_dn);
+            if (kk[u].x > kk[u].y) {  // L > U in key order: test the crossing exactly
+              const bool cross = isint[u] ? (L > U) : (L > U + P.eps_feas * d_max1abs(U));
+              if (cross) atomicOr(&s_inf[g], 1u << lane);
+            }
+          }
+          if (lane == 0 && wd[u] != 0u) atomicOr(&s_chg[g], wd[u]);
+        }
+      }
     }
   }
   __syncthreads();
@@ -781,7 +788,6 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
     vc->round = r;
     const int32_t cont = (live && !P.err) ? 1 : 0;
     vc->any_alive = cont;
-    vc->ndirty[p ^ 1] = 0;
     vc->blocks_done = 0;
     __threadfence();
     if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
@@ -1098,7 +1104,7 @@ cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
   mark(3);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   mark(4);
-  k_bact<<<num_sms * 3, kActWarps * 32, 0, st>>>(M, S);
+  k_bact<<<num_sms * 4, kActWarps * 32, 0, st>>>(M, S);
   mark(5);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   mark(6);

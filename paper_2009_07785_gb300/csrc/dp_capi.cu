@@ -860,8 +860,6 @@ int batch_state(const DevMatrix &M, int32_t Bp, std::vector<void *> &allocs, Bat
   ATRY(track_alloc(allocs, &S.nkey, 2 * n * Bp, bytes));
   ATRY(track_alloc(allocs, &S.chg[0], n * Gs, bytes));
   ATRY(track_alloc(allocs, &S.chg[1], n * Gs, bytes));
-  ATRY(track_alloc(allocs, &S.dirty[0], 2 * n * Bp, bytes));
-  ATRY(track_alloc(allocs, &S.dirty[1], 2 * n * Bp, bytes));
   ATRY(track_alloc(allocs, &S.cmask, nslots * Gs, bytes));
   ATRY(track_alloc(allocs, &S.items, G * nslots, bytes));
   ATRY(track_alloc(allocs, &S.part, split_slots * Bp, bytes));

@@ -217,7 +217,6 @@ struct BCtrl {
   int32_t err;        // 0, or a DP_ERR_* code found by the prologue
   int32_t any_alive;  // some node is still propagating
   uint32_t blocks_done;
-  int32_t ndirty[2];  // entries of the two dirty lists
   int32_t icount[kMaxGroups];  // work items of each node group this round
   double eps_int, tau_rel, eps_feas, inf_thr;
 };
@@ -226,8 +225,8 @@ struct BatchState {
   double2 *cur;         // [n*Bp] {L, U} at the start of the round
   float2 *wid;          // [n*Bp] screen widths {W_U, W_L} of those bounds
   long long *nkey;      // [2*n*Bp] next state as order-preserving keys
-  uint32_t *chg[2];     // [n*G] nodes of each group whose bounds of var j changed
-  uint32_t *dirty[2];   // [2*n*Bp] entries e = j*Bp+node improved in a round
+  uint32_t *chg[2];     // [n*Gs] nodes of each group whose bounds of var j changed
+                        // (set while a round runs, committed and cleared after)
   uint32_t *cmask;      // [nslots*G] nodes of each group that process a chunk
   int32_t *items;       // [G*nslots] chunk slots to process, one region per group
   BPartial *part;       // [nsplit_slots*Bp]
