@@ -467,6 +467,21 @@ def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3, chunk=0):
         e1.record(stream)
         torch.cuda.synchronize()
         t_batch = e0.elapsed_time(e1) / reps
+        # the same batch with the round loop in one persistent cooperative kernel
+        lo2, hi2 = torch.empty_like(lo), torch.empty_like(hi)
+        for _ in range(warmup):
+            rq = dp.dp_propagate_nodes_persistent(ctx, mat, dLB, dUB, vt, lhs, rhs, lb_out=lo2,
+                                                  ub_out=hi2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            rq = dp.dp_propagate_nodes_persistent(ctx, mat, dLB, dUB, vt, lhs, rhs, lb_out=lo2,
+                                                  ub_out=hi2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_pers = e0.elapsed_time(e1) / reps
+        assert np.array_equal(rq.rounds, r.rounds) and torch.equal(lo2, lo) and \
+            torch.equal(hi2, hi), "persistent and graph batch results differ"
         rows = [(dLB[k].contiguous(), dUB[k].contiguous()) for k in range(count)]
         o1 = torch.empty(inst.n, dtype=torch.float64, device="cuda")
         o2 = torch.empty_like(o1)
@@ -489,6 +504,8 @@ def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3, chunk=0):
                      "plain_loop_nodes_per_s": count / (t_plain * 1e-3),
                      "speedup_vs_plain_loop": t_plain / t_batch,
                      "ms_per_batch": round(t_batch, 3), "plain_loop_ms": round(t_plain, 3),
+                     "persistent_ms_per_batch": round(t_pers, 3),
+                     "persistent_speedup_vs_plain_loop": t_plain / t_pers,
                      "rounds_mean": float(r.rounds.mean()), "rounds_max": int(r.rounds.max()),
                      "infeasible_nodes": int(r.infeasible.sum()),
                      "stage_ms": {k: round(v, 3) for k, v in zip(dp.NODE_STAGES, h.kernel_ms)}}
@@ -548,6 +565,19 @@ def sets_bench(dp, ctx, stream, reps=3, warmup=3):
     e1.record(stream)
     torch.cuda.synchronize()
     t_set = e0.elapsed_time(e1) / reps
+    # the same set with the round loop in one persistent cooperative kernel
+    lo2, hi2 = torch.empty_like(lo), torch.empty_like(hi)
+    for _ in range(warmup):
+        rp = dp.dp_propagate_set_persistent(ctx, ms, *args, lb_out=lo2, ub_out=hi2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        rp = dp.dp_propagate_set_persistent(ctx, ms, *args, lb_out=lo2, ub_out=hi2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_set_p = e0.elapsed_time(e1) / reps
+    assert np.array_equal(rp.rounds, r.rounds) and torch.equal(lo2, lo) and torch.equal(hi2, hi), \
+        "persistent and graph set results differ"
     mats = [dp.Matrix(ctx, p.m, p.n, p.row_ptr, p.col, p.val, lhs=p.lhs, rhs=p.rhs) for p in ps]
     pargs = [[dev(a) for a in (p.lb, p.ub, p.vartype, p.lhs, p.rhs)] for p in ps]
     outs = [(torch.empty(p.n, dtype=torch.float64, device="cuda"),
@@ -576,6 +606,8 @@ def sets_bench(dp, ctx, stream, reps=3, warmup=3):
             "plain_loop_problems_per_s": len(ps) / (t_plain * 1e-3),
             "speedup_vs_plain_loop": t_plain / t_set,
             "ms_per_set": round(t_set, 3), "plain_loop_ms": round(t_plain, 3),
+            "persistent_ms_per_set": round(t_set_p, 3),
+            "persistent_speedup_vs_plain_loop": t_plain / t_set_p,
             "nnz_rounds_per_s": nnz_rounds / (t_set * 1e-3),
             "rounds_max": int(r.rounds.max()), "rounds_mean": float(r.rounds.mean()),
             "infeasible_problems": int(r.infeasible.sum())}

@@ -334,6 +334,24 @@ int dp_propagate_set(dp_ctx *ctx, const dp_matrix *set, const double *lb,
                      int32_t *infeasible, int32_t *rounds, int32_t *status);
 
 /*
+ * dp_propagate_set with the whole round loop in one persistent cooperative
+ * kernel (Sec. 3.7, Appendix C): every phase of every round runs in one
+ * launch, with a bounded grid barrier between phases (see
+ * dp_ctx_set_wait_limit).  Same arguments, results and return values as
+ * dp_propagate_set, plus DP_ERR_TIMEOUT if a barrier wait runs out (the
+ * context stays usable) and DP_ERR_CUDA if the device cannot launch
+ * cooperative kernels; DP_ERR_INVALID_ARG for a set loaded in the merge
+ * layout.
+ */
+int dp_propagate_set_persistent(dp_ctx *ctx, const dp_matrix *set,
+                                const double *lb, const double *ub,
+                                const uint8_t *vartype, const double *lhs,
+                                const double *rhs, const dp_params *params,
+                                double *lb_out, double *ub_out,
+                                int32_t *infeasible, int32_t *rounds,
+                                int32_t *status);
+
+/*
  * The same propagation with the round loop driven from the host: after each
  * round the control block is copied back and the stream synchronised, and
  * the host decides whether to launch the next round (the cpu_loop variant
@@ -360,8 +378,9 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *mat, const double *lb,
  * exist so that the library's bounded waits and its clean-up after a
  * failed allocation can be tested without faulting a GPU.
  *
- * dp_ctx_set_wait_limit: a block of the persistent round loop
- * (dp_propagate_persistent) waits at a grid barrier for at most `sleeps`
+ * dp_ctx_set_wait_limit: a block of a persistent round loop
+ * (dp_propagate_persistent, dp_propagate_nodes_persistent,
+ * dp_propagate_set_persistent) waits at a grid barrier for at most `sleeps`
  * sleeps of about 64 ns before it records DP_ERR_TIMEOUT and every block
  * leaves the kernel; the call then returns DP_ERR_TIMEOUT and the context
  * stays usable.  0 restores the default (2^25 sleeps, about 2 s).  Under a
@@ -477,6 +496,24 @@ int dp_propagate_nodes_hostloop(dp_ctx *ctx, const dp_matrix *mat,
                                 double *ub_out, int32_t *infeasible,
                                 int32_t *rounds, int32_t *status,
                                 float *kernel_ms, int32_t *kernel_launches);
+
+/*
+ * dp_propagate_nodes with the whole round loop in one persistent kernel (the
+ * single-kernel loop of Sec. 3.7 and Appendix C, for a batch): a
+ * cooperative launch of as many blocks as fit on the GPU at once runs every
+ * phase of every round, with a bounded grid barrier between phases (see
+ * dp_ctx_set_wait_limit) instead of kernel boundaries and no graph.  Same
+ * arguments, results and return values as dp_propagate_nodes, plus
+ * DP_ERR_TIMEOUT if a barrier wait runs out (the context stays usable) and
+ * DP_ERR_CUDA if the device cannot launch cooperative kernels.
+ */
+int dp_propagate_nodes_persistent(dp_ctx *ctx, const dp_matrix *mat,
+                                  int32_t count, const double *lb,
+                                  const double *ub, const uint8_t *vartype,
+                                  const double *lhs, const double *rhs,
+                                  const dp_params *params, double *lb_out,
+                                  double *ub_out, int32_t *infeasible,
+                                  int32_t *rounds, int32_t *status);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  The paper has no

@@ -35,7 +35,8 @@ SYMBOLS = ("dp_params_default", "dp_strerror", "dp_create", "dp_destroy", "dp_ma
            "dp_autotune", "dp_autotune_nodes", "dp_matrix_free", "dp_matrix_info", "dp_propagate",
            "dp_propagate_hostloop",
            "dp_propagate_noalloc", "dp_propagate_nodes", "dp_propagate_set",
-           "dp_propagate_persistent",
+           "dp_propagate_persistent", "dp_propagate_nodes_persistent",
+           "dp_propagate_set_persistent",
            "dp_propagate_nodes_hostloop", "dp_server_create", "dp_server_add_matrix",
            "dp_server_submit", "dp_server_poll", "dp_server_stats_get", "dp_server_clock_us",
            "dp_server_destroy", "dp_ctx_set_wait_limit", "dp_debug_fail_alloc",
@@ -115,6 +116,8 @@ def lib() -> C.CDLL:
     L.dp_propagate_set.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp, vp,
                                    vp, vp]
     L.dp_propagate_set.restype = C.c_int
+    L.dp_propagate_set_persistent.argtypes = L.dp_propagate_set.argtypes
+    L.dp_propagate_set_persistent.restype = C.c_int
     L.dp_propagate_persistent.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp,
                                           vp, C.POINTER(i32), C.POINTER(i32)]
     L.dp_propagate_persistent.restype = C.c_int
@@ -145,6 +148,8 @@ def lib() -> C.CDLL:
     L.dp_propagate_nodes.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, C.POINTER(dp_params), vp, vp,
                                      vp, vp, vp]
     L.dp_propagate_nodes.restype = C.c_int
+    L.dp_propagate_nodes_persistent.argtypes = L.dp_propagate_nodes.argtypes
+    L.dp_propagate_nodes_persistent.restype = C.c_int
     L.dp_propagate_nodes_hostloop.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp,
                                               C.POINTER(dp_params), vp, vp, vp, vp, vp,
                                               C.POINTER(C.c_float), C.POINTER(i32)]
@@ -447,6 +452,18 @@ def dp_propagate_set(ctx: Context, mset: MatrixSet, lb, ub, vartype, lhs, rhs,
                      params: dp_params | None = None, lb_out=None, ub_out=None) -> SetResult:
     """Propagates every problem of a set; arrays are the problems' arrays
     concatenated in problem order.  Per-problem flags and round counts."""
+    return _set(ctx, mset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, False)
+
+
+def dp_propagate_set_persistent(ctx: Context, mset: MatrixSet, lb, ub, vartype, lhs, rhs,
+                                params: dp_params | None = None, lb_out=None,
+                                ub_out=None) -> SetResult:
+    """dp_propagate_set with the round loop in one persistent cooperative
+    kernel; same results."""
+    return _set(ctx, mset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, True)
+
+
+def _set(ctx, mset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, persistent):
     if lb_out is None:
         lb_out = _like(lb, mset.n)
     if ub_out is None:
@@ -455,11 +472,12 @@ def dp_propagate_set(ctx: Context, mset: MatrixSet, lb, ub, vartype, lhs, rhs,
     inf = np.zeros(k, dtype=np.int32)
     rounds = np.zeros(k, dtype=np.int32)
     cap = np.zeros(k, dtype=np.int32)
-    rc = _check(lib().dp_propagate_set(ctx.handle, mset.handle, _ptr(lb), _ptr(ub), _ptr(vartype),
-                                       _ptr(lhs), _ptr(rhs),
-                                       C.byref(params) if params is not None else None,
-                                       _ptr(lb_out), _ptr(ub_out), inf.ctypes.data,
-                                       rounds.ctypes.data, cap.ctypes.data), "dp_propagate_set")
+    name = "dp_propagate_set_persistent" if persistent else "dp_propagate_set"
+    rc = _check(getattr(lib(), name)(ctx.handle, mset.handle, _ptr(lb), _ptr(ub), _ptr(vartype),
+                                     _ptr(lhs), _ptr(rhs),
+                                     C.byref(params) if params is not None else None,
+                                     _ptr(lb_out), _ptr(ub_out), inf.ctypes.data,
+                                     rounds.ctypes.data, cap.ctypes.data), name)
     return SetResult(lb_out, ub_out, inf, rounds, cap, rc)
 
 
@@ -623,16 +641,25 @@ def dp_propagate_nodes(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
     return _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, None)
 
 
+def dp_propagate_nodes_persistent(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
+                                  params: dp_params | None = None, lb_out=None,
+                                  ub_out=None) -> NodesResult:
+    """dp_propagate_nodes with the round loop in one persistent cooperative
+    kernel; same results."""
+    return _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, "persistent")
+
+
 def dp_propagate_nodes_hostloop(ctx: Context, mat: Matrix, lb, ub, vartype, lhs, rhs,
                                 params: dp_params | None = None, lb_out=None,
                                 ub_out=None) -> NodesResult:
     """dp_propagate_nodes with a host-driven round loop and per-stage
     CUDA-event timings (NodesResult.kernel_ms / kernel_launches, in the order
     of NODE_STAGES)."""
-    return _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, True)
+    return _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, "hostloop")
 
 
-def _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, hostloop):
+def _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, mode):
+    """mode: None (the graph), "hostloop" or "persistent"."""
     count = int(lb.shape[0]) if len(lb.shape) == 2 else 0
     if len(lb.shape) != 2 or tuple(ub.shape) != tuple(lb.shape) or int(lb.shape[1]) != mat.n:
         raise ValueError("lb and ub must both have shape [count, n]")
@@ -646,14 +673,15 @@ def _nodes(ctx, mat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, hostloop
     args = (ctx.handle, mat.handle, count, _ptr(lb), _ptr(ub), _ptr(vartype), _ptr(lhs),
             _ptr(rhs), C.byref(params) if params is not None else None, _ptr(lb_out),
             _ptr(ub_out), inf.ctypes.data, rounds.ctypes.data, cap.ctypes.data)
-    if hostloop:
+    if mode == "hostloop":
         ms = (C.c_float * len(NODE_STAGES))()
         cnt = (C.c_int32 * len(NODE_STAGES))()
         rc = _check(lib().dp_propagate_nodes_hostloop(*args, ms, cnt),
                     "dp_propagate_nodes_hostloop")
         return NodesResult(lb_out, ub_out, inf[:count], rounds[:count], cap[:count], rc,
                            tuple(ms), tuple(cnt))
-    rc = _check(lib().dp_propagate_nodes(*args), "dp_propagate_nodes")
+    name = "dp_propagate_nodes_persistent" if mode == "persistent" else "dp_propagate_nodes"
+    rc = _check(getattr(lib(), name)(*args), name)
     return NodesResult(lb_out, ub_out, inf[:count], rounds[:count], cap[:count], rc)
 
 

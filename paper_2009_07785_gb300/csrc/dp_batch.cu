@@ -75,14 +75,20 @@ __device__ __forceinline__ BParams load_params(const BCtrl *c) {
   return P;
 }
 
-// Bounds {L, U} of one (variable, node) entry and their screen widths;
-// read-only within a kernel.
+// Bounds {L, U} of one (variable, node) entry and their screen widths.
+// A round kernel of the graph never sees them change (read-only path); the
+// persistent loop (kCo) rewrites them between its phases, so it loads them
+// through L2, which is coherent across the grid.
+template <bool kCo>
 __device__ __forceinline__ double2 ld_bounds(const double2 *p) {
+  if (kCo) return __ldcg(p);
   double2 v;
   asm("ld.global.nc.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
   return v;
 }
+template <bool kCo>
 __device__ __forceinline__ float2 ld_widths(const float2 *p) {
+  if (kCo) return __ldcg(p);
   float2 v;
   asm("ld.global.nc.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
   return v;
@@ -159,6 +165,7 @@ __device__ __forceinline__ void act_add(double a, double2 b, float2 w, bool need
   }
 }
 
+template <bool kCo>
 __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchState &S,
                                                int64_t base, int len, int node, bool need_min,
                                                bool need_max, bool screen, const BParams &P) {
@@ -201,8 +208,8 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
     float2 w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      b[u] = ld_bounds(bp + (int64_t)j[u] * P.Bp);
-      w[u] = screen ? ld_widths(wp + (int64_t)j[u] * P.Bp) : make_float2(0.0f, 0.0f);
+      b[u] = ld_bounds<kCo>(bp + (int64_t)j[u] * P.Bp);
+      w[u] = screen ? ld_widths<kCo>(wp + (int64_t)j[u] * P.Bp) : make_float2(0.0f, 0.0f);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) act_add(a[u], b[u], w[u], need_min, need_max, screen, r);
@@ -210,8 +217,8 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
   for (; k < len; ++k) {
     const double a = __ldg(vp + (int64_t)k * kSliceW);
     const int32_t j = __ldg(cp + (int64_t)k * kSliceW);
-    const double2 b = ld_bounds(bp + (int64_t)j * P.Bp);
-    const float2 w = screen ? ld_widths(wp + (int64_t)j * P.Bp) : make_float2(0.0f, 0.0f);
+    const double2 b = ld_bounds<kCo>(bp + (int64_t)j * P.Bp);
+    const float2 w = screen ? ld_widths<kCo>(wp + (int64_t)j * P.Bp) : make_float2(0.0f, 0.0f);
     act_add(a, b, w, need_min, need_max, screen, r);
   }
   if (!screen) r.tr = r.tl = f_inf();
@@ -263,6 +270,7 @@ struct PairQueue {
 // Evaluates pairs [from, from + count) of the buffer, count <= 32, and
 // marks the entries they change in the round's change mask chg_next (one
 // atomic per mask word among the lanes).  All 32 lanes call.
+template <bool kCo>
 __device__ __forceinline__ void eval_pairs(PairQueue &pq, int from, int count,
                                            const DevMatrix &M, const BatchState &S,
                                            const BParams &P, uint32_t *chg_next) {
@@ -286,7 +294,7 @@ __device__ __forceinline__ void eval_pairs(PairQueue &pq, int from, int count,
     const double a = __ldg(M.val + off);
     const int32_t j = __ldg(M.col + off);
     const int64_t e = (int64_t)j * P.Bp + node;
-    const double2 b = ld_bounds(S.cur + e);
+    const double2 b = ld_bounds<kCo>(S.cur + e);
     const bool isint = __ldg(S.vt + j) != 0;
     if (bnnz_candidates(a, isint, b.x, b.y, info & 3u, rv, P, S.nkey + 2 * e)) {
       widx = (unsigned long long)j * P.Gs + (node >> 5);
@@ -306,6 +314,7 @@ __device__ __forceinline__ void eval_pairs(PairQueue &pq, int from, int count,
 // can tighten.  Four nonzeros are screened per step, their loads in flight
 // together; the survivors then enter the pair buffer in CSR order.  All 32
 // lanes call.
+template <bool kCo>
 __device__ __forceinline__ void chunk_candidates(const DevMatrix &M, const BatchState &S,
                                                  int64_t base, int len, int node, bool on,
                                                  int32_t row, const RowView &rv,
@@ -335,8 +344,8 @@ __device__ __forceinline__ void chunk_candidates(const DevMatrix &M, const Batch
       float2 w[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        b[u] = ld_bounds(bp + (int64_t)j[u] * P.Bp);
-        w[u] = ld_widths(wp + (int64_t)j[u] * P.Bp);
+        b[u] = ld_bounds<kCo>(bp + (int64_t)j[u] * P.Bp);
+        w[u] = ld_widths<kCo>(wp + (int64_t)j[u] * P.Bp);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -360,23 +369,24 @@ __device__ __forceinline__ void chunk_candidates(const DevMatrix &M, const Batch
       pq.n += __popc(m);
       if (pq.n >= 32) {
         pq.n -= 32;
-        eval_pairs(pq, pq.n, 32, M, S, P, chg_next);
+        eval_pairs<kCo>(pq, pq.n, 32, M, S, P, chg_next);
       }
     }
   }
 }
 
 // Evaluates what is left in the pair buffer (end of a warp's work).
+template <bool kCo>
 __device__ __forceinline__ void drain_pairs(PairQueue &pq, const DevMatrix &M,
                                             const BatchState &S, const BParams &P,
                                             uint32_t *chg_next) {
-  if (pq.n > 0) eval_pairs(pq, 0, pq.n, M, S, P, chg_next);
+  if (pq.n > 0) eval_pairs<kCo>(pq, 0, pq.n, M, S, P, chg_next);
   pq.n = 0;
 }
 
 // ------------------------------------------------------------- k_bmark --
 
-__global__ void __launch_bounds__(kThreads) k_bmark(DevMatrix M, BatchState S) {
+__device__ __forceinline__ void bmark_body(const DevMatrix &M, const BatchState &S) {
   BCtrl *ctrl = S.ctrl;
   const BParams P = load_params(ctrl);
   if (P.err) return;
@@ -447,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_bmark(DevMatrix M, BatchState S) {
 
 // All chunks of a split row get the OR of their masks (the row's activity
 // needs every chunk), and become work items.  Warp per split row.
-__global__ void __launch_bounds__(kThreads) k_bmark_split(DevMatrix M, BatchState S) {
+__device__ __forceinline__ void bmark_split_body(const DevMatrix &M, const BatchState &S) {
   BCtrl *ctrl = S.ctrl;
   const BParams P = load_params(ctrl);
   if (P.err) return;
@@ -485,10 +495,9 @@ __global__ void __launch_bounds__(kThreads) k_bmark_split(DevMatrix M, BatchStat
 
 // -------------------------------------------------------------- k_bact --
 
-// Four blocks of eight warps per SM (64 registers, a few spilled): the
-// kernel waits on gathers, and 32 resident warps hide more of that latency
-// than 24 warps without spills do (7% faster on a dense first round).
-__global__ void __launch_bounds__(kActWarps * 32, 4) k_bact(DevMatrix M, BatchState S) {
+template <bool kCo>
+__device__ __forceinline__ void bact_body(const DevMatrix &M, const BatchState &S,
+                                          PairBuf *s_pairs) {
   BCtrl *ctrl = S.ctrl;
   const BParams P = load_params(ctrl);
   if (P.err) return;
@@ -506,7 +515,6 @@ __global__ void __launch_bounds__(kActWarps * 32, 4) k_bact(DevMatrix M, BatchSt
   const int excl = incl - cnt;
   const int64_t split_slots = (int64_t)M.nslices_split * kSliceW;
   const int nw = gridDim.x * kActWarps;
-  __shared__ PairBuf s_pairs[kActWarps];
   PairQueue pq{&s_pairs[threadIdx.x >> 5], 0};
   uint32_t *chg_next = S.chg[p ^ 1];
   for (int it = blockIdx.x * kActWarps + (threadIdx.x >> 5); it < total; it += nw) {
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(kActWarps * 32, 4) k_bact(DevMatrix M, BatchSt
     const int64_t base = M.slice_off[cs / kSliceW] + (cs % kSliceW);
     const double lhs = S.lhs[row], rhs = S.rhs[row];
     const bool need_min = d_isfinite(rhs), need_max = d_isfinite(lhs);
-    const BAct r = chunk_activity(M, S, base, len, node, need_min, need_max, !exact, P);
+    const BAct r = chunk_activity<kCo>(M, S, base, len, node, need_min, need_max, !exact, P);
     if (cs < split_slots) {
       BPartial pt;
       pt.minfin = r.minfin;
@@ -547,14 +555,14 @@ __global__ void __launch_bounds__(kActWarps * 32, 4) k_bact(DevMatrix M, BatchSt
     note_nodes(S.inf_bits, g, on && infeas);
     const bool go = on && rv.act != 0;
     if (!__any_sync(kFull, go)) continue;
-    chunk_candidates(M, S, base, len, node, go, row, rv, P, pq, chg_next);
+    chunk_candidates<kCo>(M, S, base, len, node, go, row, rv, P, pq, chg_next);
   }
-  drain_pairs(pq, M, S, P, chg_next);
+  drain_pairs<kCo>(pq, M, S, P, chg_next);
 }
 
 // ---------------------------------------------------------- split rows --
 
-__global__ void __launch_bounds__(kThreads) k_bcombine(DevMatrix M, BatchState S) {
+__device__ __forceinline__ void bcombine_body(const DevMatrix &M, const BatchState &S) {
   const BParams P = load_params(S.ctrl);
   if (P.err) return;
   const int lane = threadIdx.x & 31;
@@ -613,7 +621,9 @@ __global__ void __launch_bounds__(kThreads) k_bcombine(DevMatrix M, BatchState S
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchState S) {
+template <bool kCo>
+__device__ __forceinline__ void bcand_split_body(const DevMatrix &M, const BatchState &S,
+                                                 PairBuf *s_pairs) {
   BCtrl *ctrl = S.ctrl;
   const BParams P = load_params(ctrl);
   if (P.err) return;
@@ -621,7 +631,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchS
   const int lane = threadIdx.x & 31;
   const int64_t pairs = (int64_t)M.nslices_split * kSliceW * P.G;
   const int nw = gridDim.x * (blockDim.x >> 5);
-  __shared__ PairBuf s_pairs[kThreads / 32];
   PairQueue pq{&s_pairs[threadIdx.x >> 5], 0};
   uint32_t *chg_next = S.chg[p ^ 1];
   for (int64_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < pairs; w += nw) {
@@ -648,9 +657,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchS
     rv.exact = (lenf & kExactFlag) ? 1 : 0;
     rv.act = on ? 1 : 0;
     const int64_t base = M.slice_off[cs / kSliceW] + (cs % kSliceW);
-    chunk_candidates(M, S, base, lenf & kLenMask, node, on, row, rv, P, pq, chg_next);
+    chunk_candidates<kCo>(M, S, base, lenf & kLenMask, node, on, row, rv, P, pq, chg_next);
   }
-  drain_pairs(pq, M, S, P, chg_next);
+  drain_pairs<kCo>(pq, M, S, P, chg_next);
 }
 
 // ----------------------------------------------------------- k_bfinish --
@@ -664,14 +673,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchS
 // (read by this round's marking) is cleared for reuse.  The last block to
 // arrive counts the round for every live node, ends the nodes that stopped
 // (no change, infeasible, or the cap) and sets the WHILE condition.
-__global__ void __launch_bounds__(kThreads)
-k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_cond) {
-  BCtrl *ctrl = S.ctrl;
-  const BParams P = load_params(ctrl);
+__device__ __forceinline__ void bfinish_commit(const BatchState &S, int32_t n,
+                                               const BParams &P, uint32_t *s_chg,
+                                               uint32_t *s_inf) {
   const int p = P.round & 1;
   const int lane = threadIdx.x & 31;
-  __shared__ uint32_t s_chg[kMaxGroups], s_inf[kMaxGroups];
-  __shared__ int s_last;
   if (threadIdx.x < kMaxGroups) {
     s_chg[threadIdx.x] = 0u;
     s_inf[threadIdx.x] = 0u;
@@ -739,15 +745,17 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
     if (s_chg[threadIdx.x]) atomicOr(&S.chg_bits[threadIdx.x], s_chg[threadIdx.x]);
     if (s_inf[threadIdx.x]) atomicOr(&S.inf_bits[threadIdx.x], s_inf[threadIdx.x]);
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
-    s_last = prev == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
+}
+
+// End of a round, one block, after every block's commit: counts the round
+// for every live node, ends the nodes that stopped (no change, infeasible,
+// or the cap), resets the per-round counters and sets the loop condition
+// (the graph's WHILE handle when use_cond).
+__device__ __forceinline__ void bfinish_decide(const BatchState &S, const BParams &P,
+                                               cudaGraphConditionalHandle handle,
+                                               int use_cond) {
+  BCtrl *ctrl = S.ctrl;
+  const int p = P.round & 1;
   const int32_t r = P.round + 1;
   const volatile uint32_t *chg_bits = S.chg_bits;
   const volatile uint32_t *inf_bits = S.inf_bits;
@@ -791,6 +799,122 @@ k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_co
     vc->blocks_done = 0;
     __threadfence();
     if (use_cond) cudaGraphSetConditional(handle, (unsigned)cont);
+  }
+  (void)p;
+}
+
+// ------------------------------------------------- round kernels (graph) --
+
+__global__ void __launch_bounds__(kThreads) k_bmark(DevMatrix M, BatchState S) {
+  bmark_body(M, S);
+}
+
+__global__ void __launch_bounds__(kThreads) k_bmark_split(DevMatrix M, BatchState S) {
+  bmark_split_body(M, S);
+}
+
+// Four blocks of eight warps per SM (64 registers, a few spilled): the
+// kernel waits on gathers, and 32 resident warps hide more of that latency
+// than 24 warps without spills do (7% faster on a dense first round).
+__global__ void __launch_bounds__(kActWarps * 32, 4) k_bact(DevMatrix M, BatchState S) {
+  __shared__ PairBuf s_pairs[kActWarps];
+  bact_body<false>(M, S, s_pairs);
+}
+
+__global__ void __launch_bounds__(kThreads) k_bcombine(DevMatrix M, BatchState S) {
+  bcombine_body(M, S);
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_bcand_split(DevMatrix M, BatchState S) {
+  __shared__ PairBuf s_pairs[kThreads / 32];
+  bcand_split_body<false>(M, S, s_pairs);
+}
+
+// Commit of every block, then the last block to arrive ends the round.
+__global__ void __launch_bounds__(kThreads)
+k_bfinish(BatchState S, int32_t n, cudaGraphConditionalHandle handle, int use_cond) {
+  __shared__ uint32_t s_chg[kMaxGroups], s_inf[kMaxGroups];
+  __shared__ int s_last;
+  const BParams P = load_params(S.ctrl);
+  bfinish_commit(S, n, P, s_chg, s_inf);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&S.ctrl->blocks_done, 1u);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  bfinish_decide(S, P, handle, use_cond);
+}
+
+// ------------------------------------------------ round loop (persistent) --
+
+// Grid barrier of the persistent loop over the batch's control block: as
+// the single-instance loop's, a block that waits more than `limit` sleeps of
+// 64 ns records DP_ERR_TIMEOUT and leaves, and every block returns false
+// once an error is recorded.  The fences make each phase's writes (plain
+// stores and atomics) visible to every block of the next phase.
+__device__ __forceinline__ bool bgrid_sync(BCtrl *c, long long limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = &c->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(&c->bar_count, 1u) == gridDim.x - 1) {
+      *(volatile unsigned *)&c->bar_count = 0u;  // all arrived; none leaves before gen moves
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > limit) {
+          atomicExch(&c->err, DP_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ((volatile BCtrl *)c)->err == 0;
+}
+
+// The batch's whole round loop in one cooperative launch (Sec. 3.7: one
+// kernel for all rounds).  Each phase is the body of the graph kernel of
+// the same name, grid-strided over the resident blocks, with a grid barrier
+// between phases instead of a kernel boundary; block 0 ends each round.
+// Four blocks per SM, as k_bact.
+__global__ void __launch_bounds__(kThreads, 4) k_bpersistent(DevMatrix M, BatchState S) {
+  __shared__ PairBuf s_pairs[kThreads / 32];
+  __shared__ uint32_t s_chg[kMaxGroups], s_inf[kMaxGroups];
+  BCtrl *ctrl = S.ctrl;
+  if (((volatile BCtrl *)ctrl)->err) return;  // set before the launch: uniform
+  const long long lim = ctrl->wait_limit;
+  const bool split = M.nsplit_rows > 0;
+  for (;;) {
+    bmark_body(M, S);
+    if (!bgrid_sync(ctrl, lim)) return;
+    if (split) {
+      bmark_split_body(M, S);
+      if (!bgrid_sync(ctrl, lim)) return;
+    }
+    bact_body<true>(M, S, s_pairs);
+    if (!bgrid_sync(ctrl, lim)) return;
+    if (split) {
+      bcombine_body(M, S);
+      if (!bgrid_sync(ctrl, lim)) return;
+      bcand_split_body<true>(M, S, s_pairs);
+      if (!bgrid_sync(ctrl, lim)) return;
+    }
+    const BParams P = load_params(ctrl);
+    bfinish_commit(S, M.n, P, s_chg, s_inf);
+    if (!bgrid_sync(ctrl, lim)) return;
+    if (blockIdx.x == 0) bfinish_decide(S, P, 0, 0);
+    if (!bgrid_sync(ctrl, lim)) return;
+    if (!((volatile BCtrl *)ctrl)->any_alive) return;
   }
 }
 
@@ -1073,6 +1197,20 @@ cudaError_t launch_batch_epilogue(const DevMatrix &M, const BatchState &S, int32
   int nb = (int)(tiles < (int64_t)num_sms * 16 ? tiles : (int64_t)num_sms * 16);
   k_bepilogue<<<nb, kThreads, 0, st>>>(S, M.n, count, Bp, lb_out, ub_out);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_persistent(const DevMatrix &M, const BatchState &S, int num_sms,
+                                    cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bpersistent, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  DevMatrix m = M;
+  BatchState s = S;
+  void *args[] = {&m, &s};
+  return cudaLaunchCooperativeKernel((const void *)k_bpersistent, dim3(num_sms * per_sm),
+                                     dim3(kThreads), args, 0, st);
 }
 
 cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,

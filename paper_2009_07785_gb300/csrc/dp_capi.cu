@@ -718,16 +718,30 @@ int dp_propagate_persistent(dp_ctx *ctx, const dp_matrix *cmat, const double *lb
   return end_call(ctx, mat, p, lb_out, ub_out, infeasible, rounds);
 }
 
-int dp_propagate_set(dp_ctx *ctx, const dp_matrix *cset, const double *lb, const double *ub,
-                     const uint8_t *vartype, const double *lhs, const double *rhs,
-                     const dp_params *params, double *lb_out, double *ub_out,
-                     int32_t *infeasible, int32_t *rounds, int32_t *status) {
+}  // extern "C"
+
+namespace {
+
+// One dp_propagate_set call: the round loop as the captured graph or as one
+// persistent cooperative kernel.
+int set_call(dp_ctx *ctx, const dp_matrix *cset, const double *lb, const double *ub,
+             const uint8_t *vartype, const double *lhs, const double *rhs,
+             const dp_params *params, double *lb_out, double *ub_out, int32_t *infeasible,
+             int32_t *rounds, int32_t *status, bool persistent) {
   if (!cset || cset->ninst <= 0 || !infeasible || !rounds) return DP_ERR_INVALID_ARG;
   dp_params p;
   int32_t dummy_inf = 0, dummy_rounds = 0;
   int rc = check_call(ctx, cset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, &dummy_inf,
                       &dummy_rounds, &p);
   if (rc) return rc;
+  if (persistent) {
+    if (cset->M.layout != dp::kLayoutEll) return DP_ERR_INVALID_ARG;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) !=
+            cudaSuccess ||
+        !coop)
+      return DP_ERR_CUDA;
+  }
   dp_matrix *set = const_cast<dp_matrix *>(cset);
   rc = begin_call(ctx, set, lb, ub, vartype, lhs, rhs, p);
   if (rc) return rc;
@@ -739,7 +753,12 @@ int dp_propagate_set(dp_ctx *ctx, const dp_matrix *cset, const double *lb, const
   CUDA_TRY(cudaMemsetAsync(I.done, 0, cb, st));
   CUDA_TRY(cudaMemsetAsync(I.rounds, 0, cb, st));
   CUDA_TRY(cudaMemsetAsync(I.status, 0, cb, st));
-  if (p.max_rounds > 0) CUDA_TRY(cudaGraphLaunch(set->exec, st));
+  if (p.max_rounds > 0) {
+    if (persistent)
+      CUDA_TRY(dp::launch_persistent(set->M, set->S, set->vt_ws, ctx->num_sms, st));
+    else
+      CUDA_TRY(cudaGraphLaunch(set->exec, st));
+  }
   int32_t *h = set->h_inst;
   CUDA_TRY(cudaMemcpyAsync(h, I.infeasible, cb, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(h + I.ninst, I.rounds, cb, cudaMemcpyDeviceToHost, st));
@@ -754,6 +773,27 @@ int dp_propagate_set(dp_ctx *ctx, const dp_matrix *cset, const double *lb, const
     cap |= h[2 * I.ninst + k] != 0;
   }
   return cap ? DP_CAP_HIT : DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dp_propagate_set(dp_ctx *ctx, const dp_matrix *cset, const double *lb, const double *ub,
+                     const uint8_t *vartype, const double *lhs, const double *rhs,
+                     const dp_params *params, double *lb_out, double *ub_out,
+                     int32_t *infeasible, int32_t *rounds, int32_t *status) {
+  return set_call(ctx, cset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, infeasible,
+                  rounds, status, false);
+}
+
+int dp_propagate_set_persistent(dp_ctx *ctx, const dp_matrix *cset, const double *lb,
+                                const double *ub, const uint8_t *vartype, const double *lhs,
+                                const double *rhs, const dp_params *params, double *lb_out,
+                                double *ub_out, int32_t *infeasible, int32_t *rounds,
+                                int32_t *status) {
+  return set_call(ctx, cset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, infeasible,
+                  rounds, status, true);
 }
 
 int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
@@ -1025,13 +1065,16 @@ int batch_hostloop(dp_matrix *mat, BatchWs *b, int32_t max_rounds, float *kernel
   return status;
 }
 
-// One dp_propagate_nodes call.  With `hostloop` the rounds are driven from
-// the host (one synchronisation per round) so that each stage can be timed
-// with CUDA events; the results are the same.
+// How a dp_propagate_nodes call runs its rounds: the captured graph (a
+// WHILE loop of the round kernels), the host (one synchronisation per round,
+// so that each stage can be timed with CUDA events), or one persistent
+// cooperative kernel.  The results are the same.
+enum NodesMode { kNodesGraph, kNodesHostloop, kNodesPersistent };
+
 int nodes_call(dp_ctx *ctx, const dp_matrix *cmat, int32_t count, const double *lb,
                const double *ub, const uint8_t *vartype, const double *lhs, const double *rhs,
                const dp_params *params, double *lb_out, double *ub_out, int32_t *infeasible,
-               int32_t *rounds, int32_t *status, bool hostloop, float *kernel_ms,
+               int32_t *rounds, int32_t *status, NodesMode mode, float *kernel_ms,
                int32_t *kernel_launches) {
   if (!ctx || !cmat || count < 0) return DP_ERR_INVALID_ARG;
   if (cmat->ctx != ctx || cmat->M.layout != dp::kLayoutEll) return DP_ERR_INVALID_ARG;
@@ -1088,6 +1131,7 @@ int nodes_call(dp_ctx *ctx, const dp_matrix *cmat, int32_t count, const double *
     hc->tau_rel = p.tau_rel;
     hc->eps_feas = p.eps_feas;
     hc->inf_thr = p.inf_threshold;
+    hc->wait_limit = ctx->wait_limit;
     const size_t Gs = (size_t)((Bp / 32 + 3) & ~3);
     CUDA_TRY(cudaMemcpyAsync(b->S.ctrl, hc, sizeof(*hc), cudaMemcpyHostToDevice, st));
     if (n > 0) {
@@ -1097,8 +1141,10 @@ int nodes_call(dp_ctx *ctx, const dp_matrix *cmat, int32_t count, const double *
     CUDA_TRY(dp::launch_batch_prologue(mat->M, b->S, cnt, d_lb, d_ub, d_vt, d_lhs, d_rhs,
                                        p.eps_int, p.tau_rel, p.eps_feas, p.inf_threshold,
                                        ctx->num_sms, st));
-    if (p.max_rounds > 0 && !hostloop) CUDA_TRY(cudaGraphLaunch(b->exec, st));
-    if (p.max_rounds > 0 && hostloop) {
+    if (p.max_rounds > 0 && mode == kNodesGraph) CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    if (p.max_rounds > 0 && mode == kNodesPersistent)
+      CUDA_TRY(dp::launch_batch_persistent(mat->M, b->S, ctx->num_sms, st));
+    if (p.max_rounds > 0 && mode == kNodesHostloop) {
       int r2 = batch_hostloop(mat, b, p.max_rounds, kernel_ms, kernel_launches);
       if (r2) return r2;
     }
@@ -1136,7 +1182,23 @@ extern "C" int dp_propagate_nodes(dp_ctx *ctx, const dp_matrix *mat, int32_t cou
                                   const dp_params *params, double *lb_out, double *ub_out,
                                   int32_t *infeasible, int32_t *rounds, int32_t *status) {
   return nodes_call(ctx, mat, count, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
-                    infeasible, rounds, status, false, nullptr, nullptr);
+                    infeasible, rounds, status, kNodesGraph, nullptr, nullptr);
+}
+
+extern "C" int dp_propagate_nodes_persistent(dp_ctx *ctx, const dp_matrix *mat, int32_t count,
+                                             const double *lb, const double *ub,
+                                             const uint8_t *vartype, const double *lhs,
+                                             const double *rhs, const dp_params *params,
+                                             double *lb_out, double *ub_out,
+                                             int32_t *infeasible, int32_t *rounds,
+                                             int32_t *status) {
+  if (!ctx) return DP_ERR_INVALID_ARG;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess ||
+      !coop)
+    return DP_ERR_CUDA;
+  return nodes_call(ctx, mat, count, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
+                    infeasible, rounds, status, kNodesPersistent, nullptr, nullptr);
 }
 
 extern "C" int dp_propagate_nodes_hostloop(dp_ctx *ctx, const dp_matrix *mat, int32_t count,
@@ -1152,5 +1214,5 @@ extern "C" int dp_propagate_nodes_hostloop(dp_ctx *ctx, const dp_matrix *mat, in
   if (kernel_launches)
     for (int k = 0; k < kBatchStages; ++k) kernel_launches[k] = 0;
   return nodes_call(ctx, mat, count, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
-                    infeasible, rounds, status, true, kernel_ms, kernel_launches);
+                    infeasible, rounds, status, kNodesHostloop, kernel_ms, kernel_launches);
 }

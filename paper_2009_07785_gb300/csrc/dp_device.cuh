@@ -260,6 +260,28 @@ __device__ __forceinline__ void ld_rec(const VarRec *p, double &L, double &U, fl
   WL = __int_as_float((int)((unsigned long long)w >> 32));
   flags = (uint32_t)((unsigned long long)__double_as_longlong(d3) & 0xFFFFFFFFull);
 }
+// ld_rec through L2 (coherent with the stores of the same launch), for the
+// persistent loops, which rewrite the records between their phases; the
+// read-only path of ld_rec is only valid where a kernel never sees a record
+// change.
+__device__ __forceinline__ void ld_rec_cg(const VarRec *p, double &L, double &U, float &WU,
+                                          float &WL, uint32_t &flags) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  const double2 lu = __ldcg(q), wf = __ldcg(q + 1);
+  L = lu.x;
+  U = lu.y;
+  const double d3 = wf.y;
+  long long w = __double_as_longlong(wf.x);
+  WU = __int_as_float((int)(w & 0xFFFFFFFFll));
+  WL = __int_as_float((int)((unsigned long long)w >> 32));
+  flags = (uint32_t)((unsigned long long)__double_as_longlong(d3) & 0xFFFFFFFFull);
+}
+template <bool kCo>
+__device__ __forceinline__ void ld_rec_t(const VarRec *p, double &L, double &U, float &WU,
+                                         float &WL, uint32_t &flags) {
+  if (kCo) ld_rec_cg(p, L, U, WU, WL, flags);
+  else ld_rec(p, L, U, WU, WL, flags);
+}
 
 __device__ __forceinline__ void st_rec(VarRec *p, double L, double U, float WU, float WL,
                                        uint32_t flags) {

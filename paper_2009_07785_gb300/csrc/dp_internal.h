@@ -217,6 +217,9 @@ struct BCtrl {
   int32_t err;        // 0, or a DP_ERR_* code found by the prologue
   int32_t any_alive;  // some node is still propagating
   uint32_t blocks_done;
+  uint32_t bar_count;    // persistent loop: grid-barrier arrivals
+  uint32_t bar_gen;      //   and its generation
+  long long wait_limit;  // persistent loop: sleeps a block waits at a grid barrier
   int32_t icount[kMaxGroups];  // work items of each node group this round
   double eps_int, tau_rel, eps_feas, inf_thr;
 };

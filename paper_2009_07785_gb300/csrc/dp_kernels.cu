@@ -89,7 +89,7 @@ struct QueuedNnz {
 // Evaluates kN queued nonzeros per thread (entries e0 + u*stride, u < kN,
 // those below cnt): every load of one dependence level is issued for all
 // of them before the next level, so kN chains are in flight at once.
-template <bool kMulti, int kN>
+template <bool kMulti, int kN, bool kCo = false>
 __device__ __forceinline__ void cand_entries(const DevMatrix &M, const DevState &S,
                                              const Ctrl &prm, int64_t e0, int64_t stride,
                                              int32_t cnt) {
@@ -111,7 +111,7 @@ __device__ __forceinline__ void cand_entries(const DevMatrix &M, const DevState 
   }
 #pragma unroll
   for (int u = 0; u < kN; ++u)
-    if (ok[u]) ld_rec(S.rec + q[u].j, q[u].L, q[u].U, q[u].WU, q[u].WL, q[u].fl);
+    if (ok[u]) ld_rec_t<kCo>(S.rec + q[u].j, q[u].L, q[u].U, q[u].WU, q[u].WL, q[u].fl);
 #pragma unroll
   for (int u = 0; u < kN; ++u) {
     if (!ok[u]) continue;
@@ -159,8 +159,9 @@ constexpr int kGroupWide = 4;
 
 // One slice of the round (warp-level: the 32 lanes are its 32 chunks).
 // kVal8: the coefficients come from the int8 copy (converted when used, so
-// that the prefetched loads stay in flight).
-template <bool kMulti, bool kVal8, int kG = kGroup>
+// that the prefetched loads stay in flight).  kCo: records are loaded
+// through L2 (the persistent loop).
+template <bool kMulti, bool kVal8, int kG = kGroup, bool kCo = false>
 __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &S, int slice) {
   const Ctrl *ctrl = S.ctrl;
   const int lane = threadIdx.x & 31;
@@ -229,7 +230,7 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
       a[u] = an[u];
       L[u] = U[u] = 0.0;
       WU[u] = WL[u] = 0.0f;
-      if (k + u < len) ld_rec(S.rec + jn[u], L[u], U[u], WU[u], WL[u], fl[u]);
+      if (k + u < len) ld_rec_t<kCo>(S.rec + jn[u], L[u], U[u], WU[u], WL[u], fl[u]);
     }
     if (k + kG < len) {
 #pragma unroll
@@ -735,6 +736,8 @@ __device__ __forceinline__ bool grid_sync(const DevState &S, long long limit) {
 
 // Two resident blocks per SM: the union of all phases needs more registers
 // than three blocks allow (spills), and fewer resident warps hide less latency.
+// kMulti: a problem set (per-problem termination, as the graph's kernels).
+template <bool kMulti>
 __global__ void __launch_bounds__(kPersistThreads, 2)
 k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
   if (((volatile Ctrl *)S.ctrl)->err) return;  // set before the launch: uniform
@@ -747,24 +750,26 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
   for (;;) {
     if (M.val8)
-      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, true, kGroupWide>(M, S, sl);
+      for (int sl = gw; sl < M.nslices; sl += nw)
+        round_slice<kMulti, true, kGroupWide, true>(M, S, sl);
     else
-      for (int sl = gw; sl < M.nslices; sl += nw) round_slice<false, false, kGroupWide>(M, S, sl);
+      for (int sl = gw; sl < M.nslices; sl += nw)
+        round_slice<kMulti, false, kGroupWide, true>(M, S, sl);
     if (!grid_sync(S, lim)) return;
     if (M.nsplit_rows > 0) {
-      for (int w = gw; w < M.nsplit_rows; w += nw) combine_rows<false>(M, S, w);
+      for (int w = gw; w < M.nsplit_rows; w += nw) combine_rows<kMulti>(M, S, w);
       if (!grid_sync(S, lim)) return;
       for (int sl = gw; sl < M.nslices_split; sl += nw) cand_split_slice(M, S, sl);
       if (!grid_sync(S, lim)) return;
     }
     const int32_t cnt = ((volatile Ctrl *)S.ctrl)->qcount;
-    for (int64_t e = gt; e < cnt; e += nt) cand_entries<false, 1>(M, S, prm, e, nt, cnt);
+    for (int64_t e = gt; e < cnt; e += nt) cand_entries<kMulti, 1, true>(M, S, prm, e, nt, cnt);
     if (!grid_sync(S, lim)) return;
     for (int64_t w0 = (gt >> 5) * kFinishWords; w0 < ((int64_t)M.n + 31) >> 5;
          w0 += (nt >> 5) * kFinishWords)
-      finish_words<false>(S, vartype, w0, ((int64_t)M.n + 31) >> 5, prm.eps_feas, tau_dn, eps_dn);
+      finish_words<kMulti>(S, vartype, w0, ((int64_t)M.n + 31) >> 5, prm.eps_feas, tau_dn, eps_dn);
     if (!grid_sync(S, lim)) return;
-    if (blockIdx.x == 0) decide_round<false>(S);
+    if (blockIdx.x == 0) decide_round<kMulti>(S);
     if (!grid_sync(S, lim)) return;
     if (!((volatile Ctrl *)S.ctrl)->cont) return;
   }
@@ -969,9 +974,11 @@ cudaError_t launch_round_kernels(const DevMatrix &M, const DevState &S, const ui
 
 cudaError_t launch_persistent(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,
                               int num_sms, cudaStream_t st) {
+  const void *kern = S.I.ninst > 0 ? (const void *)k_persistent<true>
+                                    : (const void *)k_persistent<false>;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent,
-                                                                kPersistThreads, 0);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   if ((e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
@@ -979,8 +986,8 @@ cudaError_t launch_persistent(const DevMatrix &M, const DevState &S, const uint8
   DevState s = S;
   const uint8_t *vt = vt_ws;
   void *args[] = {&m, &s, &vt};
-  return cudaLaunchCooperativeKernel((const void *)k_persistent, dim3(num_sms * per_sm),
-                                     dim3(kPersistThreads), args, 0, st);
+  return cudaLaunchCooperativeKernel(kern, dim3(num_sms * per_sm), dim3(kPersistThreads), args,
+                                     0, st);
 }
 
 cudaError_t launch_round_body(const DevMatrix &M, const DevState &S, const uint8_t *vt_ws,

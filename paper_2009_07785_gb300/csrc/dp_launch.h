@@ -53,6 +53,9 @@ cudaError_t launch_batch_epilogue(const DevMatrix &M, const BatchState &S, int32
 // One batched round; in a graph body (use_cond = 1) the last kernel sets
 // the WHILE condition.  With `ev` (12 events) each of the six stages (mark,
 // mark_split, act, combine, cand_split, finish) is bracketed by a pair.
+// The batch's round loop as one cooperative kernel (all rounds; no graph).
+cudaError_t launch_batch_persistent(const DevMatrix &M, const BatchState &S, int num_sms,
+                                    cudaStream_t st);
 cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
                                cudaGraphConditionalHandle handle, int use_cond,
                                int num_sms, cudaStream_t st, cudaEvent_t *ev);
