@@ -179,6 +179,14 @@ def peaks():
     return PEAK_FALLBACK_GBS, "fallback"
 
 
+def sm_max_mhz():
+    """The maximum SM clock (MEASURED_PEAKS.json, else the GB300's 2070 MHz)."""
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return float(json.loads(p.read_text()).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
 def source_sha(names):
     """Hash of the code of csrc files, comments and whitespace removed (a
     comment edit does not change what a profile capture measured)."""
@@ -509,6 +517,21 @@ def nodes_bench(dp, ctx, stream, count=256, reps=3, warmup=3, chunk=0):
                      "rounds_mean": float(r.rounds.mean()), "rounds_max": int(r.rounds.max()),
                      "infeasible_nodes": int(r.infeasible.sum()),
                      "stage_ms": {k: round(v, 3) for k, v in zip(dp.NODE_STAGES, h.kernel_ms)}}
+        if int(r.rounds.max()) == 1:
+            # one round in which every node processes every row: the activity
+            # pass's (nonzero, node) pairs against the binary64 pipe's floor
+            # for the activities alone (one FMA per nonzero, node and finite
+            # side; 2 FMAs per clock per SM at the maximum SM clock)
+            act_ms = h.kernel_ms[dp.NODE_STAGES.index("act")]
+            sides = np.isfinite(inst.lhs).astype(np.int64) + np.isfinite(inst.rhs)
+            fmas = float((np.diff(inst.row_ptr) * sides).sum()) * count
+            fp64_peak = 2.0 * torch.cuda.get_device_properties(0).multi_processor_count * \
+                sm_max_mhz() * 1e6
+            out[name]["k_bact"] = {
+                "ms": round(act_ms, 3), "nnz_node_pairs_per_s": inst.nnz * count / (act_ms * 1e-3),
+                "activity_fmas": fmas, "fp64_fma_peak_per_s": fp64_peak,
+                "fp64_floor_ms": round(fmas / fp64_peak * 1e3, 3),
+                "fp64_floor_frac": fmas / fp64_peak * 1e3 / act_ms}
     mat.close()
     mat_p.close()
     return out
