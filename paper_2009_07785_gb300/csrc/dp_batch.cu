@@ -178,38 +178,29 @@ __device__ __forceinline__ BAct chunk_activity(const DevMatrix &M, const BatchSt
   const double2 *bp = S.cur + node;
   const float2 *wp = S.wid + node;
   int k = 0;
-  // software-pipelined: the next group's values and columns are fetched
-  // while this group's bounds are gathered
-  double an[4];
+  // software-pipelined: the next group's columns are fetched while this
+  // group's bounds are gathered; its values load beside the gathers
   int32_t jn[4];
   if (len >= 4) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      an[u] = __ldg(vp + (int64_t)u * kSliceW);
-      jn[u] = __ldg(cp + (int64_t)u * kSliceW);
-    }
+    for (int u = 0; u < 4; ++u) jn[u] = __ldg(cp + (int64_t)u * kSliceW);
   }
   for (; k + 4 <= len; k += 4) {
-    double a[4];
     int32_t j[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      a[u] = an[u];
-      j[u] = jn[u];
-    }
+    for (int u = 0; u < 4; ++u) j[u] = jn[u];
     if (k + 8 <= len) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        an[u] = __ldg(vp + (int64_t)(k + 4 + u) * kSliceW);
-        jn[u] = __ldg(cp + (int64_t)(k + 4 + u) * kSliceW);
-      }
+      for (int u = 0; u < 4; ++u) jn[u] = __ldg(cp + (int64_t)(k + 4 + u) * kSliceW);
     }
     double2 b[4];
     float2 w[4];
+    double a[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       b[u] = ld_bounds<kCo>(bp + (int64_t)j[u] * P.Bp);
       w[u] = screen ? ld_widths<kCo>(wp + (int64_t)j[u] * P.Bp) : make_float2(0.0f, 0.0f);
+      a[u] = __ldg(vp + (int64_t)(k + u) * kSliceW);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) act_add(a[u], b[u], w[u], need_min, need_max, screen, r);
