@@ -1,5 +1,6 @@
 // Batched propagation of branch-and-bound nodes: many bound vectors over
-// one matrix in one graph-driven round loop.  The paper propagates one
+// one matrix in one graph-driven round loop (or, k_bpersistent, in one
+// persistent cooperative kernel running the same phases).  The paper propagates one
 // problem per call and notes (Sec. 5) that after branching a solver
 // propagates from an already propagated state with a few bound changes;
 // a throughput device is fed by running many such nodes at once.
@@ -26,16 +27,17 @@
 // Round kernels (graph body):
 //   k_bmark        thread per chunk: the nodes that must process it (OR of
 //                  the change masks of its variables); work lists per group
-//   k_bmark_split  warp per split row: all chunks of a split row get the
+//   k_bmark_split  block per split row: all chunks of a split row get the
 //                  row's mask
 //   k_bact         warp per work item: activities; for whole rows also
 //                  Step 2, the binary32 screen and the candidates with
 //                  filtered 64-bit atomics
-//   k_bcombine     warp per (split row, group): sums chunk partials in
-//                  chunk order, Step 2 and screen thresholds
+//   k_bcombine     block per (split row, group): sums chunk partials in a
+//                  fixed order, Step 2 and screen thresholds
 //   k_bcand_split  warp per (split chunk, group): candidates of split rows
-//   k_bfinish      thread per improved entry: commit, crossing test, change
-//                  masks; the last block ends nodes and sets the condition
+//   k_bfinish      warp per 32 change-mask words, lane per node: commit,
+//                  crossing test; the last block ends nodes and sets the
+//                  condition
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cfloat>
@@ -447,19 +449,23 @@ __device__ __forceinline__ void bmark_body(const DevMatrix &M, const BatchState 
 }
 
 // All chunks of a split row get the OR of their masks (the row's activity
-// needs every chunk), and become work items.  Warp per split row.
+// needs every chunk), and become work items.  Block per split row.
 __device__ __forceinline__ void bmark_split_body(const DevMatrix &M, const BatchState &S) {
   BCtrl *ctrl = S.ctrl;
   const BParams P = load_params(ctrl);
   if (P.err) return;
-  const int lane = threadIdx.x & 31;
+  constexpr int kW = kThreads / 32;
+  __shared__ uint4 s_m[kW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nslots = S.nslots;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < M.nsplit_rows; s += nw) {
+  // block per split row (block-uniform loop): the block's threads stride
+  // over the row's chunks, a row of hundreds of chunks would otherwise be
+  // one warp's serial chain
+  for (int s = blockIdx.x; s < M.nsplit_rows; s += gridDim.x) {
     const int32_t q0 = M.split_cbeg[s], q1 = M.split_cbeg[s + 1];
     for (int gq = 0; gq < P.Gs; gq += 4) {
       uint4 m = make_uint4(0u, 0u, 0u, 0u);
-      for (int32_t q = q0 + lane; q < q1; q += 32)
+      for (int32_t q = q0 + threadIdx.x; q < q1; q += kThreads)
         m = or4(m, *reinterpret_cast<const uint4 *>(S.cmask + (int64_t)M.split_cidx[q] * P.Gs + gq));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -468,13 +474,19 @@ __device__ __forceinline__ void bmark_split_body(const DevMatrix &M, const Batch
         m.z |= __shfl_xor_sync(kFull, m.z, o);
         m.w |= __shfl_xor_sync(kFull, m.w, o);
       }
-      for (int32_t q = q0 + lane; q < q1; q += 32)
+      if (lane == 0) s_m[warp] = m;
+      __syncthreads();
+      m = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int k = 0; k < kW; ++k) m = or4(m, s_m[k]);
+      __syncthreads();  // s_m is reused by the next group quad
+      for (int32_t q = q0 + threadIdx.x; q < q1; q += kThreads)
         *reinterpret_cast<uint4 *>(S.cmask + (int64_t)M.split_cidx[q] * P.Gs + gq) = m;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int g = gq + u;
-        if (g >= P.G || word4(m, u) == 0u) continue;  // uniform
-        for (int32_t qb = q0; qb < q1; qb += 32) {
+        if (g >= P.G || word4(m, u) == 0u) continue;  // block-uniform
+        for (int32_t qb = q0 + warp * 32; qb < q1; qb += kThreads) {  // warp-uniform
           const int32_t q = qb + lane;
           warp_append<int32_t>(q < q1, q < q1 ? M.split_cidx[q] : 0,
                                S.items + (int64_t)g * nslots, &ctrl->icount[g]);
@@ -553,62 +565,87 @@ __device__ __forceinline__ void bact_body(const DevMatrix &M, const BatchState &
 
 // ---------------------------------------------------------- split rows --
 
+// Block per (split row, node group), block-uniform loop: each of the eight
+// warps sums a contiguous eighth of the row's chunk partials in chunk order
+// (four pieces' loads in flight at a time), and warp 0 adds the eight sums in
+// warp order, a fixed association whatever the scheduling; then Step 2 and
+// the screen thresholds of the row for the group's nodes.
 __device__ __forceinline__ void bcombine_body(const DevMatrix &M, const BatchState &S) {
   const BParams P = load_params(S.ctrl);
   if (P.err) return;
-  const int lane = threadIdx.x & 31;
+  constexpr int kW = kThreads / 32;
+  __shared__ BPartial s_sum[kW][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t pairs = (int64_t)M.nsplit_rows * P.G;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < pairs; w += nw) {
+  for (int64_t w = blockIdx.x; w < pairs; w += gridDim.x) {
     const int s = (int)(w / P.G), g = (int)(w % P.G);
     const int32_t q0 = M.split_cbeg[s], q1 = M.split_cbeg[s + 1];
     const int64_t c0 = M.split_cidx[q0];
     const uint32_t mask = S.cmask[c0 * P.Gs + g];
-    if (mask == 0u) {
-      if (lane == 0) S.srow_act[(int64_t)s * P.Gs + g] = 0u;
+    if (mask == 0u) {  // block-uniform
+      if (threadIdx.x == 0) S.srow_act[(int64_t)s * P.Gs + g] = 0u;
       continue;
     }
     const int node = g * 32 + lane;
-    const bool on = ((mask >> lane) & 1u) != 0u;
-    const int32_t row = M.split_row[s];
-    RowView rv;
-    rv.minfin = rv.maxfin = 0.0;
-    rv.mininf = rv.maxinf = 0;
-    float tr = -f_inf(), tl = -f_inf();
+    BPartial acc;
+    acc.minfin = acc.maxfin = 0.0;
+    acc.mininf = acc.maxinf = 0;
+    acc.tr = acc.tl = -f_inf();
     auto add = [&](const BPartial &pt) {
-      rv.minfin += pt.minfin;
-      rv.maxfin += pt.maxfin;
-      rv.mininf += pt.mininf;
-      rv.maxinf += pt.maxinf;
-      tr = fmaxf(tr, pt.tr);
-      tl = fmaxf(tl, pt.tl);
+      acc.minfin += pt.minfin;
+      acc.maxfin += pt.maxfin;
+      acc.mininf += pt.mininf;
+      acc.maxinf += pt.maxinf;
+      acc.tr = fmaxf(acc.tr, pt.tr);
+      acc.tl = fmaxf(acc.tl, pt.tl);
     };
-    // the row's pieces in order; four pieces' loads in flight at a time (a
-    // row of hundreds of pieces would otherwise pay one load latency each)
-    int32_t q = q0;
-    for (; q + 4 <= q1; q += 4) {
+    const int32_t span = (q1 - q0 + kW - 1) / kW;
+    const int32_t qa = min(q1, q0 + warp * span), qb = min(q1, qa + span);
+    int32_t q = qa;
+    for (; q + 4 <= qb; q += 4) {
       BPartial pt[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) pt[u] = S.part[(int64_t)M.split_cidx[q + u] * P.Bp + node];
 #pragma unroll
       for (int u = 0; u < 4; ++u) add(pt[u]);
     }
-    for (; q < q1; ++q) add(S.part[(int64_t)M.split_cidx[q] * P.Bp + node]);
-    rv.lhs = S.lhs[row];
-    rv.rhs = S.rhs[row];
-    rv.exact = (M.chunk_len[c0] & kExactFlag) ? 1 : 0;
-    const bool infeas = row_sides_eval(rv, tr, tl, P.eps_feas);
-    note_nodes(S.inf_bits, g, on && infeas);
-    BRowTot t;
-    t.minfin = rv.minfin;
-    t.maxfin = rv.maxfin;
-    t.mininf = rv.mininf;
-    t.maxinf = rv.maxinf;
-    t.thr_r = rv.thr_r;
-    t.thr_l = rv.thr_l;
-    S.rowtot[(int64_t)s * P.Bp + node] = t;
-    const unsigned act = __ballot_sync(kFull, on && rv.act != 0);
-    if (lane == 0) S.srow_act[(int64_t)s * P.Gs + g] = act;
+    for (; q < qb; ++q) add(S.part[(int64_t)M.split_cidx[q] * P.Bp + node]);
+    s_sum[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      const bool on = ((mask >> lane) & 1u) != 0u;
+      const int32_t row = M.split_row[s];
+      RowView rv;
+      rv.minfin = rv.maxfin = 0.0;
+      rv.mininf = rv.maxinf = 0;
+      float tr = -f_inf(), tl = -f_inf();
+#pragma unroll
+      for (int k = 0; k < kW; ++k) {
+        const BPartial &pt = s_sum[k][lane];
+        rv.minfin += pt.minfin;
+        rv.maxfin += pt.maxfin;
+        rv.mininf += pt.mininf;
+        rv.maxinf += pt.maxinf;
+        tr = fmaxf(tr, pt.tr);
+        tl = fmaxf(tl, pt.tl);
+      }
+      rv.lhs = S.lhs[row];
+      rv.rhs = S.rhs[row];
+      rv.exact = (M.chunk_len[c0] & kExactFlag) ? 1 : 0;
+      const bool infeas = row_sides_eval(rv, tr, tl, P.eps_feas);
+      note_nodes(S.inf_bits, g, on && infeas);
+      BRowTot tt;
+      tt.minfin = rv.minfin;
+      tt.maxfin = rv.maxfin;
+      tt.mininf = rv.mininf;
+      tt.maxinf = rv.maxinf;
+      tt.thr_r = rv.thr_r;
+      tt.thr_l = rv.thr_l;
+      S.rowtot[(int64_t)s * P.Bp + node] = tt;
+      const unsigned act = __ballot_sync(kFull, on && rv.act != 0);
+      if (lane == 0) S.srow_act[(int64_t)s * P.Gs + g] = act;
+    }
+    __syncthreads();  // s_sum is reused by the block's next pair
   }
 }
 
@@ -1228,8 +1265,8 @@ cudaError_t launch_batch_round(const DevMatrix &M, const BatchState &S,
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   mark(2);
   if (split)
-    k_bmark_split<<<grid_for((int64_t)M.nsplit_rows * 32, kThreads, num_sms * 4), kThreads, 0,
-                    st>>>(M, S);
+    k_bmark_split<<<grid_for((int64_t)M.nsplit_rows * kThreads, kThreads, num_sms * 4), kThreads,
+                    0, st>>>(M, S);
   mark(3);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   mark(4);
