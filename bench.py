@@ -411,7 +411,8 @@ def per_round_times(dp, ctx, mat, d_in, max_rounds=100):
     rows = []
     for r in range(1, max_rounds + 1):
         res = dp.dp_propagate_hostloop(ctx, mat, lb, ub, *d_in[2:], params=p1, timing=True)
-        rows.append({"round": r, **{k: round(res.kernel_ms[i] * 1e3, 1)
+        # kernel times in us, keyed by kernel name ("round" is k_round)
+        rows.append({"index": r, **{k: round(res.kernel_ms[i] * 1e3, 1)
                                     for i, k in enumerate(dp.KERNELS)}})
         lb, ub = res.lb.clone(), res.ub.clone()
         if res.status != dp.DP_CAP_HIT or res.infeasible:
