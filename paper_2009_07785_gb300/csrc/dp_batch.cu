@@ -787,6 +787,9 @@ __device__ __forceinline__ void bfinish_decide(const BatchState &S, const BParam
   const int32_t r = P.round + 1;
   const volatile uint32_t *chg_bits = S.chg_bits;
   const volatile uint32_t *inf_bits = S.inf_bits;
+  int live = 0;
+  // warp-uniform trip count (Bp and the block are multiples of 32): the
+  // lanes of a warp are the 32 nodes of one group, whose live mask is a ballot
   for (int node = threadIdx.x; node < P.Bp; node += blockDim.x) {
     int32_t d = S.node_done[node];
     if (!d && !P.err) {
@@ -802,17 +805,11 @@ __device__ __forceinline__ void bfinish_decide(const BatchState &S, const BParam
       }
     }
     S.node_done[node] = d;
-  }
-  __syncthreads();
-  int live = 0;
-  for (int g = threadIdx.x; g < P.Gs; g += blockDim.x) {
-    uint32_t w = 0u;
-    if (g < P.G)
-      for (int b = 0; b < 32; ++b)
-        if (!S.node_done[g * 32 + b]) w |= 1u << b;
-    S.alive[g] = w;
+    const unsigned w = __ballot_sync(kFull, d == 0);
+    if ((threadIdx.x & 31) == 0) S.alive[node >> 5] = w;
     live |= w != 0u;
   }
+  for (int g = P.G + (int)threadIdx.x; g < P.Gs; g += blockDim.x) S.alive[g] = 0u;
   live = __syncthreads_or(live);
   if (threadIdx.x < kMaxGroups) {
     ctrl->icount[threadIdx.x] = 0;
