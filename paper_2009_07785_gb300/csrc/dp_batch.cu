@@ -379,6 +379,41 @@ __device__ __forceinline__ void drain_pairs(PairQueue &pq, const DevMatrix &M,
 
 // ------------------------------------------------------------- k_bmark --
 
+// The nodes of one node-group quad [gq, gq + 4) that must process a chunk
+// (the OR of its variables' change masks, every node in its first round),
+// restricted to live nodes.  `len` nonzeros from `base`, lane-strided by
+// `step` from `k0` (a thread walks all of them with k0 = 0, step = 1).
+__device__ __forceinline__ uint4 chunk_mask(const DevMatrix &M, const BatchState &S,
+                                            const BParams &P, const uint32_t *chg, int64_t base,
+                                            int len, int k0, int step, int gq) {
+  uint4 m = make_uint4(0u, 0u, 0u, 0u);
+  int k = k0;
+  // four elements' loads in flight at a time
+  for (; k + 3 * step < len; k += 4 * step) {
+    int32_t j[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) j[u] = M.col[base + (int64_t)(k + u * step) * kSliceW];
+    uint4 w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      w[u] = *reinterpret_cast<const uint4 *>(chg + (int64_t)j[u] * P.Gs + gq);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = or4(m, w[u]);
+  }
+  for (; k < len; k += step) {
+    const int32_t j = M.col[base + (int64_t)k * kSliceW];
+    m = or4(m, *reinterpret_cast<const uint4 *>(chg + (int64_t)j * P.Gs + gq));
+  }
+  return m;
+}
+
+__device__ __forceinline__ uint4 live_mask(const BatchState &S, uint4 m, int gq) {
+  const uint4 al = *reinterpret_cast<const uint4 *>(S.alive + gq);
+  const uint4 fr = *reinterpret_cast<const uint4 *>(S.fresh + gq);
+  m = or4(m, fr);
+  return make_uint4(m.x & al.x, m.y & al.y, m.z & al.z, m.w & al.w);
+}
+
 __device__ __forceinline__ void bmark_body(const DevMatrix &M, const BatchState &S) {
   BCtrl *ctrl = S.ctrl;
   const BParams P = load_params(ctrl);
@@ -388,7 +423,40 @@ __device__ __forceinline__ void bmark_body(const DevMatrix &M, const BatchState 
   const uint32_t *chg = S.chg[p];
   const int64_t nslots = S.nslots;
   const int64_t split_slots = (int64_t)M.nslices_split * kSliceW;
-  for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < nslots;
+  const int lane = threadIdx.x & 31;
+  // chunks of split rows (long): a warp per chunk, lanes strided over its
+  // nonzeros; k_bmark_split makes them work items
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t cs = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       cs < split_slots; cs += nwarps) {
+    const int32_t row = M.chunk_row[cs];
+    if (row < 0) continue;  // warp-uniform
+    const int len = M.chunk_len[cs] & kLenMask;
+    const int64_t base = M.slice_off[cs / kSliceW] + (cs % kSliceW);
+    const bool used = d_isfinite(S.lhs[row]) || d_isfinite(S.rhs[row]);
+    for (int gq = 0; gq < P.Gs; gq += 4) {
+      uint4 m = make_uint4(0u, 0u, 0u, 0u);
+      if (used) {
+        if (first) {
+          m = make_uint4(kFull, kFull, kFull, kFull);
+        } else {
+          m = chunk_mask(M, S, P, chg, base, len, lane, 32, gq);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            m.x |= __shfl_xor_sync(kFull, m.x, o);
+            m.y |= __shfl_xor_sync(kFull, m.y, o);
+            m.z |= __shfl_xor_sync(kFull, m.z, o);
+            m.w |= __shfl_xor_sync(kFull, m.w, o);
+          }
+        }
+        m = live_mask(S, m, gq);
+      }
+      if (lane == 0) *reinterpret_cast<uint4 *>(S.cmask + cs * P.Gs + gq) = m;
+    }
+  }
+  // whole rows: a thread per chunk (block-uniform loop: warp_append needs
+  // every lane)
+  for (int64_t c0 = split_slots + (int64_t)blockIdx.x * blockDim.x; c0 < nslots;
        c0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cs = c0 + threadIdx.x;
     int32_t row = -1, len = 0;
@@ -403,46 +471,22 @@ __device__ __forceinline__ void bmark_body(const DevMatrix &M, const BatchState 
         used = d_isfinite(S.lhs[row]) || d_isfinite(S.rhs[row]);
       }
     }
-    const bool split = cs < split_slots;
     for (int gq = 0; gq < P.Gs; gq += 4) {
       uint4 m = make_uint4(0u, 0u, 0u, 0u);
       if (row >= 0) {
-        if (!used) {
-        } else if (first) {
-          m = make_uint4(kFull, kFull, kFull, kFull);
-        } else {
-          // four elements' loads in flight at a time
-          int k = 0;
-          for (; k + 4 <= len; k += 4) {
-            int32_t j[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) j[u] = M.col[base + (int64_t)(k + u) * kSliceW];
-            uint4 w[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              w[u] = *reinterpret_cast<const uint4 *>(chg + (int64_t)j[u] * P.Gs + gq);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) m = or4(m, w[u]);
-          }
-          for (; k < len; ++k) {
-            const int32_t j = M.col[base + (int64_t)k * kSliceW];
-            m = or4(m, *reinterpret_cast<const uint4 *>(chg + (int64_t)j * P.Gs + gq));
-          }
+        if (used) {
+          m = first ? make_uint4(kFull, kFull, kFull, kFull)
+                    : chunk_mask(M, S, P, chg, base, len, 0, 1, gq);
+          m = live_mask(S, m, gq);
         }
-        const uint4 al = *reinterpret_cast<const uint4 *>(S.alive + gq);
-        const uint4 fr = *reinterpret_cast<const uint4 *>(S.fresh + gq);
-        m = or4(m, fr);
-        m = make_uint4(m.x & al.x, m.y & al.y, m.z & al.z, m.w & al.w);
         *reinterpret_cast<uint4 *>(S.cmask + cs * P.Gs + gq) = m;
       }
-      if (!split) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int g = gq + u;
-          if (g < P.G)  // uniform
-            warp_append<int32_t>(used && word4(m, u) != 0u, (int32_t)cs,
-                                 S.items + (int64_t)g * nslots, &ctrl->icount[g]);
-        }
+      for (int u = 0; u < 4; ++u) {
+        const int g = gq + u;
+        if (g < P.G)  // uniform
+          warp_append<int32_t>(used && word4(m, u) != 0u, (int32_t)cs,
+                               S.items + (int64_t)g * nslots, &ctrl->icount[g]);
       }
     }
   }
