@@ -25,8 +25,9 @@
 // were then applied or rejected against bounds that have not moved since.
 //
 // Round kernels (graph body):
-//   k_bmark        thread per chunk: the nodes that must process it (OR of
-//                  the change masks of its variables); work lists per group
+//   k_bmark        thread per chunk (warp per split-row chunk): the nodes
+//                  that must process it (OR of the change masks of its
+//                  variables); work lists per group
 //   k_bmark_split  block per split row: all chunks of a split row get the
 //                  row's mask
 //   k_bact         warp per work item: activities; for whole rows also
