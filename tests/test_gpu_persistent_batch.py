@@ -136,3 +136,14 @@ def test_set_persistent_wait_runs_out_and_context_survives(gpu):
         p = dp.dp_propagate_set_persistent(ctx, ms, *arrays)
         assert np.array_equal(ref.rounds, p.rounds)
         assert torch.equal(ref.lb, p.lb) and torch.equal(ref.ub, p.ub)
+
+
+def test_nodes_persistent_two_launches(gpu):
+    """1100 nodes: more than one launch's 1024, run as two persistent launches."""
+    dp, ctx = gpu
+    inst = synth.tiny()
+    LB, UB = synth.node_bounds(inst, 1100, seed=9)
+    with dp.Matrix(ctx, inst.m, inst.n, inst.row_ptr, inst.col, inst.val) as mat:
+        args = node_args(inst, LB, UB)
+        same_nodes(dp.dp_propagate_nodes(ctx, mat, *args),
+                   dp.dp_propagate_nodes_persistent(ctx, mat, *args))
