@@ -20,6 +20,7 @@
 #include "dp_launch.h"
 #include "dp_objects.h"
 #include "../../include/domprop.h"
+#include "dp_trace.h"
 
 namespace dp {
 namespace {
@@ -297,6 +298,7 @@ void dp_matrix_free(dp_matrix *mat) {
 int dp_matrix_load(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                    const int64_t *row_ptr, const int32_t *col_idx,
                    const double *val, int32_t chunk, dp_matrix **out) {
+  dp::TraceRange trace_range("dp_matrix_load");
   return dp_matrix_load_sides(ctx, m, n, nnz, row_ptr, col_idx, val, chunk, nullptr, nullptr,
                               out);
 }
@@ -444,6 +446,7 @@ int dp_matrix_load_sides(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                          const int64_t *row_ptr, const int32_t *col_idx, const double *val,
                          int32_t chunk, const double *lhs, const double *rhs,
                          dp_matrix **out) {
+  dp::TraceRange trace_range("dp_matrix_load_sides");
   return load_impl(ctx, m, n, nnz, row_ptr, col_idx, val, chunk, lhs, rhs, nullptr, nullptr,
                    out);
 }
@@ -452,6 +455,7 @@ int dp_matrix_load_merge(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                          const int64_t *row_ptr, const int32_t *col_idx, const double *val,
                          int32_t items_per_thread, const double *lhs, const double *rhs,
                          dp_matrix **out) {
+  dp::TraceRange trace_range("dp_matrix_load_merge");
   if (items_per_thread < 4 || items_per_thread > 4096) {
     if (out) *out = nullptr;
     return DP_ERR_INVALID_ARG;
@@ -464,6 +468,7 @@ int dp_matrix_load_set(dp_ctx *ctx, int32_t count, const int32_t *m, const int32
                        const int64_t *const *row_ptr, const int32_t *const *col_idx,
                        const double *const *val, int32_t chunk, const double *const *lhs,
                        const double *const *rhs, dp_matrix **out) {
+  dp::TraceRange trace_range("dp_matrix_load_set");
   if (!ctx || !out || count <= 0 || !m || !n || !row_ptr || !col_idx || !val)
     return DP_ERR_INVALID_ARG;
   *out = nullptr;
@@ -569,6 +574,7 @@ int dp_matrix_info(const dp_matrix *mat, int32_t *m, int32_t *n, int64_t *nnz,
 }
 
 int dp_matrix_access_floor(dp_ctx *ctx, const dp_matrix *mat, int32_t reps, float *us) {
+  dp::TraceRange trace_range("dp_matrix_access_floor");
   if (!ctx || !mat || !us || reps < 1 || mat->ctx != ctx) return DP_ERR_INVALID_ARG;
   if (mat->M.layout != dp::kLayoutEll) return DP_ERR_INVALID_ARG;
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -686,6 +692,7 @@ int dp_propagate(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
                  const double *ub, const uint8_t *vartype, const double *lhs,
                  const double *rhs, const dp_params *params, double *lb_out,
                  double *ub_out, int32_t *infeasible, int32_t *rounds) {
+  dp::TraceRange trace_range("dp_propagate");
   dp_params p;
   int rc = check_call(ctx, cmat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
                       infeasible, rounds, &p);
@@ -701,6 +708,7 @@ int dp_propagate_persistent(dp_ctx *ctx, const dp_matrix *cmat, const double *lb
                             const double *ub, const uint8_t *vartype, const double *lhs,
                             const double *rhs, const dp_params *params, double *lb_out,
                             double *ub_out, int32_t *infeasible, int32_t *rounds) {
+  dp::TraceRange trace_range("dp_propagate_persistent");
   dp_params p;
   int rc = check_call(ctx, cmat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
                       infeasible, rounds, &p);
@@ -783,6 +791,7 @@ int dp_propagate_set(dp_ctx *ctx, const dp_matrix *cset, const double *lb, const
                      const uint8_t *vartype, const double *lhs, const double *rhs,
                      const dp_params *params, double *lb_out, double *ub_out,
                      int32_t *infeasible, int32_t *rounds, int32_t *status) {
+  dp::TraceRange trace_range("dp_propagate_set");
   return set_call(ctx, cset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, infeasible,
                   rounds, status, false);
 }
@@ -792,6 +801,7 @@ int dp_propagate_set_persistent(dp_ctx *ctx, const dp_matrix *cset, const double
                                 const double *rhs, const dp_params *params, double *lb_out,
                                 double *ub_out, int32_t *infeasible, int32_t *rounds,
                                 int32_t *status) {
+  dp::TraceRange trace_range("dp_propagate_set_persistent");
   return set_call(ctx, cset, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out, infeasible,
                   rounds, status, true);
 }
@@ -802,6 +812,7 @@ int dp_propagate_hostloop(dp_ctx *ctx, const dp_matrix *cmat, const double *lb,
                           const dp_params *params, double *lb_out,
                           double *ub_out, int32_t *infeasible, int32_t *rounds,
                           float *kernel_ms, int32_t *kernel_launches) {
+  dp::TraceRange trace_range("dp_propagate_hostloop");
   dp_params p;
   int rc = check_call(ctx, cmat, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
                       infeasible, rounds, &p);
@@ -1114,6 +1125,7 @@ int nodes_call(dp_ctx *ctx, const dp_matrix *cmat, int32_t count, const double *
   }
   bool any_cap = false;
   for (int32_t s0 = 0; s0 < count; s0 += per) {
+    dp::TraceRange batch_range("node batch launch");
     const int32_t cnt = count - s0 < per ? count - s0 : per;
     const int32_t Bp = (cnt + 31) / 32 * 32;
     const size_t off = (size_t)s0 * (size_t)n, len = (size_t)cnt * (size_t)n;
@@ -1181,6 +1193,7 @@ extern "C" int dp_propagate_nodes(dp_ctx *ctx, const dp_matrix *mat, int32_t cou
                                   const double *lhs, const double *rhs,
                                   const dp_params *params, double *lb_out, double *ub_out,
                                   int32_t *infeasible, int32_t *rounds, int32_t *status) {
+  dp::TraceRange trace_range("dp_propagate_nodes");
   return nodes_call(ctx, mat, count, lb, ub, vartype, lhs, rhs, params, lb_out, ub_out,
                     infeasible, rounds, status, kNodesGraph, nullptr, nullptr);
 }
@@ -1192,6 +1205,7 @@ extern "C" int dp_propagate_nodes_persistent(dp_ctx *ctx, const dp_matrix *mat, 
                                              double *lb_out, double *ub_out,
                                              int32_t *infeasible, int32_t *rounds,
                                              int32_t *status) {
+  dp::TraceRange trace_range("dp_propagate_nodes_persistent");
   if (!ctx) return DP_ERR_INVALID_ARG;
   int coop = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess ||
@@ -1209,6 +1223,7 @@ extern "C" int dp_propagate_nodes_hostloop(dp_ctx *ctx, const dp_matrix *mat, in
                                            int32_t *infeasible, int32_t *rounds,
                                            int32_t *status, float *kernel_ms,
                                            int32_t *kernel_launches) {
+  dp::TraceRange trace_range("dp_propagate_nodes_hostloop");
   if (kernel_ms)
     for (int k = 0; k < kBatchStages; ++k) kernel_ms[k] = 0.0f;
   if (kernel_launches)

@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "../../include/domprop.h"
+#include "dp_trace.h"
 
 namespace {
 
@@ -260,6 +261,7 @@ extern "C" int dp_propagate_noalloc(int device, void *cuda_stream, int32_t m, in
                                     const double *rhs, const dp_params *params,
                                     double *lb_out, double *ub_out, int32_t *infeasible,
                                     int32_t *rounds) {
+  dp::TraceRange trace_range("dp_propagate_noalloc");
   if (!infeasible || !rounds || m < 0 || n < 0 || nnz < 0) return DP_ERR_INVALID_ARG;
   if (n > DP_NOALLOC_MAX_VARS) return DP_ERR_INVALID_ARG;
   dp_params p;

@@ -36,6 +36,7 @@
 #include "dp_launch.h"
 #include "dp_objects.h"
 #include "../../include/domprop.h"
+#include "dp_trace.h"
 
 namespace {
 
@@ -500,6 +501,7 @@ int dp_server_create(dp_ctx *ctx, const dp_server_config *cfg, dp_server **out) 
 
 int dp_server_add_matrix(dp_server *s, const dp_matrix *mat, const uint8_t *vartype,
                          const double *lhs, const double *rhs, int32_t *matrix_id) {
+  dp::TraceRange trace_range("dp_server_add_matrix");
   if (!s || !mat || !matrix_id || mat->ctx != s->ctx) return DP_ERR_INVALID_ARG;
   if (mat->M.layout != dp::kLayoutEll) return DP_ERR_INVALID_ARG;
   const int32_t m = mat->M.m, n = mat->M.n;
@@ -540,6 +542,7 @@ int dp_server_add_matrix(dp_server *s, const dp_matrix *mat, const uint8_t *vart
 
 int dp_server_submit(dp_server *s, int32_t matrix_id, const double *lb, const double *ub,
                      double *lb_out, double *ub_out, uint64_t tag, double arrival_us) {
+  dp::TraceRange trace_range("dp_server_submit");
   if (!s) return DP_ERR_INVALID_ARG;
   Request r;
   const Lane *L = nullptr;
@@ -574,6 +577,7 @@ int dp_server_submit(dp_server *s, int32_t matrix_id, const double *lb, const do
 
 int dp_server_poll(dp_server *s, dp_completion *out, int32_t max, int32_t *count,
                    int32_t wait_us) {
+  dp::TraceRange trace_range("dp_server_poll");
   if (!s || !count || max < 0 || (max > 0 && !out)) return DP_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> g(s->mu);
   if (s->done.empty() && wait_us > 0 && !s->error)

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/domprop.h"
+#include "dp_trace.h"
 
 extern "C" int dp_autotune(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                            const int64_t *row_ptr, const int32_t *col_idx, const double *val,
@@ -20,6 +21,7 @@ extern "C" int dp_autotune(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                            const double *lhs, const double *rhs, const dp_params *params,
                            int32_t rounds, dp_tune_entry *entries, int32_t max_entries,
                            int32_t *count, dp_tune_entry *best) {
+  dp::TraceRange trace_range("dp_autotune");
   if (!ctx || !best || max_entries < 0 || (max_entries > 0 && !entries) ||
       (m > 0 && !row_ptr))
     return DP_ERR_INVALID_ARG;
@@ -92,6 +94,7 @@ extern "C" int dp_autotune_nodes(dp_ctx *ctx, int32_t m, int32_t n, int64_t nnz,
                                  const double *rhs, const dp_params *params,
                                  dp_tune_entry *entries, int32_t max_entries, int32_t *count,
                                  dp_tune_entry *best) {
+  dp::TraceRange trace_range("dp_autotune_nodes");
   if (!ctx || !best || nodes < 1 || max_entries < 0 || (max_entries > 0 && !entries) ||
       (m > 0 && !row_ptr))
     return DP_ERR_INVALID_ARG;
