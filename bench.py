@@ -336,7 +336,10 @@ def parity_vs_oracle(inst, g_lb, g_ub, g_rounds, g_infeasible, o):
         with np.errstate(invalid="ignore"):
             d = np.abs(g - r)
         tol = np.maximum(PARITY_ABS, PARITY_REL * np.abs(r))
-        ok = np.where(isint, same, same | (d <= tol))
+        # the tolerance applies where both are finite: an infinite bound on
+        # one side only is a different result
+        both_fin = np.isfinite(g) & np.isfinite(r)
+        ok = np.where(isint, same, same | (both_fin & (d <= tol)))
         bad += int((~ok).sum())
         fin = np.isfinite(g) & np.isfinite(r) & ~isint
         if fin.any():

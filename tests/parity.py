@@ -16,11 +16,15 @@ ABS = 1e-12
 
 
 def close_cont(g, o, err):
-    both_inf = (g == o)
+    """Equal (including equal infinities), or both finite and within the
+    tolerance: an infinite bound on one side only is a different result,
+    never a rounding difference (the relative tolerance of an infinite
+    oracle value would otherwise be infinite)."""
+    same = (g == o)
     tol = np.maximum(np.maximum(ABS, REL * np.abs(o)), err)
     with np.errstate(invalid="ignore"):
-        fin = np.abs(g - o) <= tol
-    return both_inf | fin
+        fin = np.isfinite(g) & np.isfinite(o) & (np.abs(g - o) <= tol)
+    return same | fin
 
 
 def compare_bounds(g_lb, g_ub, o_lb, o_ub, vartype, lb_err=None, ub_err=None, lb_tie=None,
