@@ -302,7 +302,7 @@ __device__ __forceinline__ void round_slice(const DevMatrix &M, const DevState &
   } else {
     rv.lhs = rv.rhs = 0.0;
   }
-  warp_enqueue<kSliceW>(rv, t, mininf, maxinf, len, c, sbase + lane, M, M.col, S);
+  warp_enqueue<kSliceW, kCo>(rv, t, mininf, maxinf, len, c, sbase + lane, M, M.col, S);
 }
 
 template <bool kMulti, int kRoundWarps, bool kVal8>
@@ -510,6 +510,7 @@ k_combine(DevMatrix M, DevState S) {
 // --------------------------------------------------------- k_cand_split --
 
 // Candidates of the active split rows' chunks of one slice (warp-level).
+template <bool kCo = false>
 __device__ __forceinline__ void cand_split_slice(const DevMatrix &M, const DevState &S,
                                                  int slice) {
   const int lane = threadIdx.x & 31;
@@ -545,7 +546,7 @@ __device__ __forceinline__ void cand_split_slice(const DevMatrix &M, const DevSt
     }
   }
   const int64_t sbase = M.slice_off[slice];
-  warp_enqueue<kSliceW>(rv, t, cmin, cmax, len, c, sbase + lane, M, M.col, S);
+  warp_enqueue<kSliceW, kCo>(rv, t, cmin, cmax, len, c, sbase + lane, M, M.col, S);
 }
 
 template <int kRoundWarps>
@@ -759,7 +760,7 @@ k_persistent(DevMatrix M, DevState S, const uint8_t *vartype) {
     if (M.nsplit_rows > 0) {
       for (int w = gw; w < M.nsplit_rows; w += nw) combine_rows<kMulti>(M, S, w);
       if (!grid_sync(S, lim)) return;
-      for (int sl = gw; sl < M.nslices_split; sl += nw) cand_split_slice(M, S, sl);
+      for (int sl = gw; sl < M.nslices_split; sl += nw) cand_split_slice<true>(M, S, sl);
       if (!grid_sync(S, lim)) return;
     }
     const int32_t cnt = ((volatile Ctrl *)S.ctrl)->qcount;

@@ -53,8 +53,9 @@ __device__ __forceinline__ int warp_reserve(int c, int32_t *counter) {
 // lane's slot in the slice, stride 32; CSR rows: the row's offset, stride
 // 1).  All 32 lanes must call this (warp collectives).  Returns whether the
 // lane's chunk needed the full re-read (done here for its first mylen
-// slots).
-template <int kStride>
+// slots).  kCo: records are loaded through L2 (the persistent loop, which
+// rewrites them between its phases).
+template <int kStride, bool kCo = false>
 __device__ __forceinline__ bool warp_enqueue(const RowView &mine, const Top2 &t, int chunk_mininf,
                                              int chunk_maxinf, int32_t mylen, int64_t chunk_slot,
                                              int64_t elem0, const DevMatrix &M,
@@ -137,7 +138,7 @@ __device__ __forceinline__ bool warp_enqueue(const RowView &mine, const Top2 &t,
       a[u] = an[u];
       L[u] = U[u] = 0.0;
       WU[u] = WL[u] = 0.0f;
-      if (k + u < len) ld_rec(S.rec + jn[u], L[u], U[u], WU[u], WL[u], fl[u]);
+      if (k + u < len) ld_rec_t<kCo>(S.rec + jn[u], L[u], U[u], WU[u], WL[u], fl[u]);
     }
     if (k + 4 < maxlen) fetch(k + 4);
     unsigned sd[4];
