@@ -147,3 +147,42 @@ def test_nodes_persistent_two_launches(gpu):
         args = node_args(inst, LB, UB)
         same_nodes(dp.dp_propagate_nodes(ctx, mat, *args),
                    dp.dp_propagate_nodes_persistent(ctx, mat, *args))
+
+
+def test_nodes_persistent_edges(gpu):
+    """Crossing input bounds, empty rows (one infeasible), a matrix without
+    rows, and a NaN input: the persistent loop ends where the graph ends."""
+    dp, ctx = gpu
+    rng = np.random.default_rng(17)
+    inst = synth.small_random(rng, 200, 150, maxlen=6)
+    LB, UB = synth.node_bounds(inst, 40, seed=4)
+    ints = np.flatnonzero(inst.vartype == 1)
+    LB[3, ints[0]] = UB[3, ints[0]] + 1.0
+    rp = np.concatenate([inst.row_ptr, [inst.row_ptr[-1]] * 2]).astype(np.int64)
+    e = synth.Instance("empty_rows", inst.m + 2, inst.n, rp, inst.col, inst.val, inst.lb, inst.ub,
+                       inst.vartype, np.concatenate([inst.lhs, [-np.inf, -np.inf]]),
+                       np.concatenate([inst.rhs, [1.0, -1.0]]), inst.xstar)
+    for q in (inst, e):
+        with dp.Matrix(ctx, q.m, q.n, q.row_ptr, q.col, q.val) as mat:
+            args = node_args(q, LB, UB)
+            g = dp.dp_propagate_nodes(ctx, mat, *args)
+            p = dp.dp_propagate_nodes_persistent(ctx, mat, *args)
+            same_nodes(g, p)
+            assert p.infeasible[3] == 1
+    n = 50
+    lb, ub = np.zeros((33, n)), np.ones((33, n))
+    with dp.Matrix(ctx, 0, n, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0)) as mat:
+        args = [dev(lb), dev(ub), dev(np.zeros(n, np.uint8)), dev(np.zeros(0)), dev(np.zeros(0))]
+        same_nodes(dp.dp_propagate_nodes(ctx, mat, *args),
+                   dp.dp_propagate_nodes_persistent(ctx, mat, *args))
+    t = synth.tiny(m=100, n=80)
+    LB, UB = synth.node_bounds(t, 40, seed=2)
+    LB[37, 5] = np.nan
+    with dp.Matrix(ctx, t.m, t.n, t.row_ptr, t.col, t.val) as mat:
+        with pytest.raises(dp.DomPropError) as ei:
+            dp.dp_propagate_nodes_persistent(ctx, mat, *node_args(t, LB, UB))
+        assert ei.value.code == dp.DP_ERR_NAN_INPUT
+        LB[37, 5] = 0.0
+        args = node_args(t, LB, UB)
+        same_nodes(dp.dp_propagate_nodes(ctx, mat, *args),
+                   dp.dp_propagate_nodes_persistent(ctx, mat, *args))
